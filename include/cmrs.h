@@ -1,0 +1,178 @@
+/*
+ * cmrs.h -- C ABI of libcmrs, Compressed Multi-Row Storage (CMRS) sparse
+ * matrix-vector products on NVIDIA GB300 (sm_103a).
+ *
+ * Method: Koza, Matyka, Szkoda, Miroslaw, "Compressed Multi-Row Storage
+ * Format for Sparse Matrices on Graphics Processing Units" (arXiv:1203.2946).
+ *
+ * Conventions for every entry point
+ *   - Return value: CMRS_OK (0) or one of the CMRS_ERR_* codes below;
+ *     cmrs_error_string() names it.  No C++ exception, abort or exit crosses
+ *     this boundary.
+ *   - Memory: the caller owns every array.  Pointers documented as "device"
+ *     must point to device memory of the current CUDA device (for example
+ *     torch tensors); pointers documented as "host" to host memory.  The
+ *     library never allocates user-visible arrays and never frees anything it
+ *     did not allocate; scratch space ("workspace") is a device buffer the
+ *     caller provides, sized by the matching *_workspace query.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Work is enqueued asynchronously on it; an entry point
+ *     synchronises only where its comment says so.
+ *   - Sizes and indices are int32; rows, cols and nnz must be < 2^31.
+ *   - A workspace must not be used by two calls that may run at the same time
+ *     (for example on two streams); results are then undefined.
+ */
+#ifndef CMRS_H
+#define CMRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define CMRS_OK 0
+#define CMRS_ERR_ARG 1          /* null pointer, negative size, bad enum, etc. */
+#define CMRS_ERR_HEIGHT 2       /* strip height outside 1..32 */
+#define CMRS_ERR_COL_OVERFLOW 3 /* cols > 2^(32 - bits): column does not fit the packed word */
+#define CMRS_ERR_CSR_INVALID 4  /* RowPtr not a valid CRS row pointer, or a column outside [0, cols) */
+#define CMRS_ERR_CUDA 5         /* a CUDA runtime call failed; cmrs_last_cuda_error() has the code */
+#define CMRS_ERR_UNSUPPORTED 6  /* valid request this build does not implement (e.g. variant on sorted strips) */
+#define CMRS_ERR_WORKSPACE 7    /* workspace pointer null/misaligned or smaller than its query returned */
+#define CMRS_ERR_TIMEOUT 8      /* a bounded in-kernel wait gave up; the output is not valid */
+
+/* ---- value storage forms ------------------------------------------------
+ * CMRS_F64    double Val[nnz]
+ * CMRS_F32    float Val[nnz] (round to nearest even from the input)
+ * CMRS_BF16   uint16 Val[nnz]: BF16 = round-to-nearest-even of the FP32 value
+ * CMRS_BF16X2 split pair: hi[nnz] = BF16(v) at byte 0, lo[nnz] = BF16(v - hi)
+ *             at byte 2 * cmrs_pad8(nnz); the represented value is hi + lo.
+ * The paper stores float or double (Section 6.2); the BF16 forms are this
+ * library's own and cut the bytes streamed per entry.  SpMV with CMRS_F64
+ * takes double x and y and accumulates in double; every other form takes
+ * float x and y and accumulates in float. */
+#define CMRS_F64 0
+#define CMRS_F32 1
+#define CMRS_BF16 2
+#define CMRS_BF16X2 3
+
+/* ---- flags --------------------------------------------------------------- */
+/* Section 4, fourth optimisation: entries of each strip ordered by column
+ * (stable: equal columns keep their CRS order). */
+#define CMRS_SORTED 1u
+
+/* ---- SpMV kernel variants -------------------------------------------------
+ * Every variant computes the same y = A x; they differ in how threads are
+ * mapped onto strips (Section 4 gives one warp per strip).
+ *   CMRS_VARIANT_ROW    one thread per row; a CTA stages the strips of 128
+ *                       consecutive rows into shared memory with bulk async
+ *                       copies and each thread walks its row there.  Needs
+ *                       unsorted strips.  Best for regular rows.
+ *   CMRS_VARIANT_STRIP  Algorithm 1 of Section 4: one warp per strip, lanes
+ *                       stride through the strip and accumulate per-row
+ *                       partial sums in a shared-memory buffer buf[row][lane],
+ *                       then a lane reduction.  Works on sorted strips.
+ *   CMRS_VARIANT_MERGE  equal-work tiles of nonzeros: each thread owns a run
+ *                       of consecutive entries, rows that cross thread or
+ *                       tile boundaries are joined afterwards in a fixed
+ *                       order.  Needs unsorted strips.  Best for skewed rows.
+ *   CMRS_VARIANT_AUTO   (-1) ROW, or STRIP for sorted strips. */
+#define CMRS_VARIANT_AUTO (-1)
+#define CMRS_VARIANT_ROW 0
+#define CMRS_VARIANT_STRIP 1
+#define CMRS_VARIANT_MERGE 2
+#define CMRS_NUM_VARIANTS 3
+
+/* A CMRS matrix: a view of caller-owned device arrays (Section 3).
+ *   strips     = ceil(rows / height)
+ *   strip_ptr  [strips + 1] device int32: StripPtr, StripPtr[strips] = nnz
+ *   col_packed [nnz] device uint32: (column << bits) | RowInStrip (Section 4);
+ *              bits = cmrs_bits_for_height(height)
+ *   val        device array of the storage form `dtype`
+ *   max_strip_nnz  longest strip, or -1 if unknown (cmrs_from_csr fills it) */
+typedef struct cmrs_matrix {
+  int32_t rows, cols, nnz, height, strips, bits;
+  uint32_t flags;
+  int32_t dtype;
+  int32_t max_strip_nnz;
+  const int32_t *strip_ptr;
+  const uint32_t *col_packed;
+  const void *val;
+} cmrs_matrix;
+
+/* Name of a status code (static string, never NULL). */
+const char *cmrs_error_string(int status);
+
+/* The cudaError_t of the last CUDA failure seen by this thread (0 if none). */
+int cmrs_last_cuda_error(void);
+
+/* Bits of RowInStrip packed under the column: the paper uses 4 for heights up
+ * to 16 (Section 4); heights 17..32 need 5.  Returns max(4, ceil(log2 h)), or
+ * -1 for h outside 1..32.  Host only, pure. */
+int cmrs_bits_for_height(int height);
+
+/* Byte offset of the lo half of a CMRS_BF16X2 array: 2 * cmrs_pad8(nnz). */
+int64_t cmrs_pad8(int64_t nnz);
+
+/* Bytes of a value array of `nnz` entries in storage form `dtype`, or -1. */
+int64_t cmrs_val_bytes(int64_t nnz, int dtype);
+
+/* ---- conversion CRS -> CMRS (Section 3, packing Section 4) ---------------
+ * Inputs (device): row_ptr[rows+1], col_ind[nnz] (int32), val_in[nnz] of type
+ * val_in_dtype (CMRS_F64 or CMRS_F32).
+ * Computes StripPtr[j] = RowPtr[j*height] (j < strips), StripPtr[strips] =
+ * nnz; packed[k] = (col << bits) | (row(k) mod height); the values converted
+ * to `dtype`; with CMRS_SORTED each strip is stably sorted by column.
+ * Outputs (device): strip_ptr_out[strips+1], col_packed_out[nnz],
+ * val_out (cmrs_val_bytes(nnz, dtype) bytes).  If `out` is not NULL it is
+ * filled with a view of the outputs (host struct).
+ * Validation: height 1..32 (CMRS_ERR_HEIGHT), cols <= 2^(32-bits)
+ * (CMRS_ERR_COL_OVERFLOW) on the host; RowPtr monotone with RowPtr[0] = 0 and
+ * RowPtr[rows] = nnz and 0 <= col < cols on the device (CMRS_ERR_CSR_INVALID).
+ * Invalid input never makes a kernel read or write outside the given arrays.
+ * Synchronises `stream` once, at the end, to read the device status word.
+ * workspace: >= cmrs_from_csr_workspace() bytes, 256-byte aligned. */
+int cmrs_from_csr_workspace(int rows, int nnz, int height, uint32_t flags, int dtype, size_t *bytes);
+int cmrs_from_csr(int rows, int cols, int nnz, const int32_t *row_ptr, const int32_t *col_ind,
+                  const void *val_in, int val_in_dtype, int height, uint32_t flags, int dtype,
+                  int32_t *strip_ptr_out, uint32_t *col_packed_out, void *val_out,
+                  void *workspace, size_t workspace_bytes, void *stream, cmrs_matrix *out);
+
+/* ---- conversion CMRS -> CRS (the inverse "to and from" of Section 3) -----
+ * RowPtr[s*height + r] = StripPtr[s] + #{entries of strip s with RowInStrip
+ * < r}, RowPtr[rows] = nnz; within a row, entries keep their strip order (for
+ * a sorted matrix each row comes out in column order); col = packed >> bits.
+ * Outputs (device): row_ptr_out[rows+1], col_ind_out[nnz], val_out in A's
+ * storage form (may be NULL to skip values).  Asynchronous; an entry whose
+ * RowInStrip names a row >= rows sets a status the next call does not read:
+ * pass a CMRS matrix built by cmrs_from_csr or one that is valid.
+ * workspace: >= cmrs_to_csr_workspace() bytes (may be 0 and NULL). */
+int cmrs_to_csr_workspace(const cmrs_matrix *A, size_t *bytes);
+int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *col_ind_out, void *val_out,
+                void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- SpMV, y = A x (Section 4, Algorithm 1) ------------------------------
+ * x: device [cols], y: device [rows], double for CMRS_F64 else float.  y is
+ * overwritten (rows without entries get 0).  A's arrays are trusted (as built
+ * by cmrs_from_csr): no validation of their contents and no synchronisation;
+ * writes are still kept inside y.  variant: CMRS_VARIANT_*.  ROW and MERGE
+ * need col_packed and val 16-byte aligned (CMRS_ERR_ARG otherwise).
+ * workspace: >= cmrs_spmv_workspace() bytes, 256-byte aligned (may be NULL
+ * when the query returns 0).  The result depends only on A, x and the variant
+ * (fixed summation order, no atomics on values): repeated calls give
+ * bit-identical y. */
+int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes);
+int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant,
+              void *workspace, size_t workspace_bytes, void *stream);
+
+/* Error status left by the last bounded in-kernel wait on this device's
+ * status word inside `workspace` (CMRS_OK or CMRS_ERR_TIMEOUT).  Reads device
+ * memory synchronously on `stream`. */
+int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMRS_H */

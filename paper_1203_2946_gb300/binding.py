@@ -1,0 +1,213 @@
+"""Thin ctypes binding of libcmrs (include/cmrs.h), same entry-point names.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device arrays are torch CUDA tensors (torch supplies device memory
+and streams); `stream=None` means torch's current stream.  Importing this
+module loads libcmrs.so and raises if it is missing: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcmrs.so")
+
+CMRS_OK = 0
+CMRS_F64, CMRS_F32, CMRS_BF16, CMRS_BF16X2 = 0, 1, 2, 3
+CMRS_SORTED = 1
+CMRS_VARIANT_AUTO, CMRS_VARIANT_ROW, CMRS_VARIANT_STRIP, CMRS_VARIANT_MERGE = -1, 0, 1, 2
+VARIANTS = {"row": 0, "strip": 1, "merge": 2}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "bf16x2": 3}
+_STORED = {0: torch.float64, 1: torch.float32, 2: torch.int16, 3: torch.int16}
+_XTYPE = {0: torch.float64, 1: torch.float32, 2: torch.float32, 3: torch.float32}
+
+
+class CmrsError(RuntimeError):
+    def __init__(self, code, where=""):
+        msg = lib().cmrs_error_string(code).decode()
+        if code == 5:
+            msg += " (cudaError %d)" % lib().cmrs_last_cuda_error()
+        super().__init__("%s: %s" % (where, msg) if where else msg)
+        self.code = code
+
+
+class cmrs_matrix(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("strips", ctypes.c_int32), ("bits", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("dtype", ctypes.c_int32), ("max_strip_nnz", ctypes.c_int32),
+                ("strip_ptr", ctypes.c_void_p), ("col_packed", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcmrs.so is not built (run __graft_entry__.build() or "
+                               "python paper_1203_2946_gb300/build.py); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, u, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t
+        M = ctypes.POINTER(cmrs_matrix)
+        sig = {
+            "cmrs_error_string": ([i], ctypes.c_char_p),
+            "cmrs_last_cuda_error": ([], i),
+            "cmrs_bits_for_height": ([i], i),
+            "cmrs_pad8": ([ctypes.c_int64], ctypes.c_int64),
+            "cmrs_val_bytes": ([ctypes.c_int64, i], ctypes.c_int64),
+            "cmrs_from_csr_workspace": ([i, i, i, u, i, ctypes.POINTER(sz)], i),
+            "cmrs_from_csr": ([i, i, i, vp, vp, vp, i, i, u, i, vp, vp, vp, vp, sz, vp, M], i),
+            "cmrs_to_csr_workspace": ([M, ctypes.POINTER(sz)], i),
+            "cmrs_to_csr": ([M, vp, vp, vp, vp, sz, vp], i),
+            "cmrs_spmv_workspace": ([M, i, ctypes.POINTER(sz)], i),
+            "cmrs_spmv": ([M, vp, vp, i, vp, sz, vp], i),
+            "cmrs_spmv_check": ([M, i, vp, vp], i),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Entry points this binding expects libcmrs to export."""
+    lib()
+    return sorted(n for n in dir(_lib) if n.startswith("cmrs_"))
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _check(rc, where):
+    if rc != CMRS_OK:
+        raise CmrsError(rc, where)
+
+
+def workspace(nbytes, device="cuda"):
+    """A zero-filled, 256-byte aligned device workspace (torch allocations are)."""
+    t = torch.zeros(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    assert t.data_ptr() % 256 == 0
+    return t
+
+
+class Matrix:
+    """A CMRS matrix whose arrays are torch tensors kept alive with the struct."""
+
+    def __init__(self, struct, strip_ptr, col_packed, val):
+        self.struct = struct
+        self.strip_ptr = strip_ptr
+        self.col_packed = col_packed
+        self.val = val
+        self._spmv_ws = {}
+
+    @property
+    def rows(self):
+        return self.struct.rows
+
+    @property
+    def cols(self):
+        return self.struct.cols
+
+    @property
+    def nnz(self):
+        return self.struct.nnz
+
+    @property
+    def height(self):
+        return self.struct.height
+
+    @property
+    def dtype(self):
+        return self.struct.dtype
+
+    @property
+    def x_dtype(self):
+        return _XTYPE[self.struct.dtype]
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+    def spmv_workspace(self, variant):
+        if variant not in self._spmv_ws:
+            n = ctypes.c_size_t()
+            _check(lib().cmrs_spmv_workspace(self.ref(), variant, ctypes.byref(n)), "cmrs_spmv_workspace")
+            self._spmv_ws[variant] = workspace(n.value, self.col_packed.device)
+        return self._spmv_ws[variant]
+
+
+def cmrs_from_csr(row_ptr, col_ind, val, cols, height, flags=0, dtype=CMRS_F64, stream=None):
+    """CRS (device int32 row_ptr, col_ind; float64 or float32 val) -> Matrix."""
+    dev = row_ptr.device
+    rows = row_ptr.numel() - 1
+    nnz = col_ind.numel()
+    assert row_ptr.dtype == torch.int32 and col_ind.dtype == torch.int32
+    in_dt = {torch.float64: CMRS_F64, torch.float32: CMRS_F32}[val.dtype]
+    strips = (rows + height - 1) // height if height > 0 else 0
+    sp = torch.empty(strips + 1, dtype=torch.int32, device=dev)
+    pk = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    vb = lib().cmrs_val_bytes(nnz, dtype)
+    if vb < 0:
+        raise CmrsError(1, "cmrs_val_bytes")
+    vout = torch.empty(max(vb, 16), dtype=torch.uint8, device=dev)
+    n = ctypes.c_size_t()
+    _check(lib().cmrs_from_csr_workspace(rows, nnz, height, flags, dtype, ctypes.byref(n)), "cmrs_from_csr_workspace")
+    ws = workspace(n.value, dev)
+    m = cmrs_matrix()
+    rc = lib().cmrs_from_csr(rows, cols, nnz, _ptr(row_ptr), _ptr(col_ind), _ptr(val), in_dt, height, flags, dtype,
+                             _ptr(sp), _ptr(pk), _ptr(vout), _ptr(ws), n.value, _stream(stream), ctypes.byref(m))
+    _check(rc, "cmrs_from_csr")
+    return Matrix(m, sp, pk, vout)
+
+
+def cmrs_spmv(A: Matrix, x, y=None, variant=CMRS_VARIANT_AUTO, workspace_tensor=None, stream=None):
+    """y = A x on the device; y is allocated if not given and returned."""
+    if y is None:
+        y = torch.empty(A.rows, dtype=A.x_dtype, device=x.device)
+    ws = workspace_tensor if workspace_tensor is not None else A.spmv_workspace(variant)
+    rc = lib().cmrs_spmv(A.ref(), _ptr(x), _ptr(y), variant, _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "cmrs_spmv")
+    return y
+
+
+def cmrs_spmv_check(A: Matrix, variant=CMRS_VARIANT_AUTO, stream=None):
+    ws = A.spmv_workspace(variant)
+    _check(lib().cmrs_spmv_check(A.ref(), variant, _ptr(ws), _stream(stream)), "cmrs_spmv_check")
+
+
+def cmrs_to_csr(A: Matrix, with_values=True, stream=None):
+    dev = A.col_packed.device
+    rp = torch.empty(A.rows + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
+    vb = lib().cmrs_val_bytes(A.nnz, A.dtype)
+    vo = torch.empty(max(vb, 16), dtype=torch.uint8, device=dev) if with_values else None
+    n = ctypes.c_size_t()
+    _check(lib().cmrs_to_csr_workspace(A.ref(), ctypes.byref(n)), "cmrs_to_csr_workspace")
+    ws = workspace(n.value, dev)
+    rc = lib().cmrs_to_csr(A.ref(), _ptr(rp), _ptr(ci), _ptr(vo) if with_values else ctypes.c_void_p(0), _ptr(ws),
+                           n.value, _stream(stream))
+    _check(rc, "cmrs_to_csr")
+    return rp, ci[:A.nnz], vo
+
+
+def stored_values(A: Matrix):
+    """The value array viewed as its storage type (BF16X2: hi then lo halves, int16 bits)."""
+    nnz = A.nnz
+    dt = _STORED[A.dtype]
+    if A.dtype == CMRS_BF16X2:
+        pad = lib().cmrs_pad8(nnz)
+        w = A.val.view(torch.int16)
+        return torch.cat([w[:nnz], w[pad:pad + nnz]])
+    return A.val.view(dt)[:nnz]

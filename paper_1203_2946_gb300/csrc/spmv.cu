@@ -1,0 +1,645 @@
+// y = A x on the CMRS format (Section 4, Algorithm 1), three thread mappings.
+//
+// GB300 design notes.  FP64 issue rate on this part is about 1/58 of FP32
+// (measured 1.2 TFLOP/s), so at HBM speed an FP64 SpMV can afford about one
+// FP64 instruction per nonzero.  The ROW and MERGE mappings therefore keep
+// each row's sum in one thread's register (one FMA per nonzero, no per-lane
+// buffer, no lane reduction); the STRIP mapping is Algorithm 1 as the paper
+// states it (per-lane row buffers + reduction) and costs 31*height extra adds
+// per strip.  Nonzero streams are copied into shared memory by the bulk-copy
+// engine (cp.async.bulk, mbarrier completion, L2 evict-first) two stages
+// ahead of the threads that use them.
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace cmrs {
+namespace {
+
+constexpr int kRowThreads = 128;  // ROW: one CTA = 128 consecutive rows
+constexpr int kRowCap = 4096;     // ROW: entries per shared-memory stage
+constexpr int kMergeThreads = 128;
+constexpr int kMergeE = 15;  // MERGE: entries per thread; odd, so that a warp's shared loads hit 32 banks
+constexpr int kMergeTile = kMergeThreads * kMergeE;
+constexpr int kStripWarps = 8;
+constexpr int kStages = 2;
+
+enum : uint8_t { F_HEAD = 1, F_TAIL = 2, F_THROUGH = 4 };
+
+// Rows crossing a MERGE tile boundary: each tile leaves the partial sum of the
+// row it starts inside (head) and of the row that runs past its end (tail).
+struct TileRec {
+  int32_t head_row, head_flag;  // head_flag: 0 none, 1 row ends in this tile, 2 row spans the whole tile
+  double head_sum;
+  int32_t tail_row, tail_flag;  // tail_flag: 1 if a row starts here and continues past the tile
+  double tail_sum;
+};
+
+struct StageInfo {
+  long long a8;
+  int staged;
+  int pad;
+};
+
+template <int DT>
+struct Stage {
+  typedef typename Form<DT>::Stored S;
+  static constexpr bool kSplit = DT == CMRS_BF16X2;
+  static constexpr size_t al(size_t b) { return (b + 127) & ~size_t(127); }
+  static constexpr size_t colp_bytes(int cap) { return al((size_t)(cap + 8) * 4); }
+  static constexpr size_t val_bytes(int cap) { return al((size_t)(cap + 8) * sizeof(S)); }
+  static constexpr size_t bytes(int cap) { return colp_bytes(cap) + val_bytes(cap) * (kSplit ? 2 : 1); }
+};
+
+// One thread: copy entries [ea, eb) of the three streams into a stage.  The
+// bulk copy covers the 8-entry-aligned body [a8, e8) (16-byte aligned for all
+// forms); entries past the last full 8-group of the array are loaded by this
+// thread, so nothing outside the arrays is read.
+template <int DT>
+__device__ void issue_stage(long long ea, long long eb, long long nnz, const uint32_t *packed,
+                            const typename Form<DT>::Stored *hi, const typename Form<DT>::Stored *lo, char *stage,
+                            int cap, uint64_t *bar, uint64_t pol, StageInfo *info) {
+  typedef typename Form<DT>::Stored S;
+  const long long a8 = ea & ~7LL, nnz8 = nnz & ~7LL;
+  long long e8 = (eb + 7) & ~7LL;
+  if (e8 > nnz8) e8 = nnz8;
+  if (e8 < a8) e8 = a8;
+  uint32_t *sc = reinterpret_cast<uint32_t *>(stage);
+  S *sh = reinterpret_cast<S *>(stage + Stage<DT>::colp_bytes(cap));
+  S *sl = reinterpret_cast<S *>(stage + Stage<DT>::colp_bytes(cap) + Stage<DT>::val_bytes(cap));
+  for (long long k = e8; k < eb; ++k) {
+    sc[k - a8] = packed[k];
+    sh[k - a8] = hi[k];
+    if (Stage<DT>::kSplit) sl[k - a8] = lo[k];
+  }
+  info->a8 = a8;
+  info->staged = 1;
+  const uint32_t cnt = (uint32_t)(e8 - a8);
+  fence_proxy_async();
+  mbar_arrive_expect_tx(bar, cnt * (4u + (uint32_t)sizeof(S) * (Stage<DT>::kSplit ? 2u : 1u)));
+  if (cnt) {
+    bulk_g2s(sc, packed + a8, cnt * 4u, bar, pol);
+    bulk_g2s(sh, hi + a8, cnt * (uint32_t)sizeof(S), bar, pol);
+    if (Stage<DT>::kSplit) bulk_g2s(sl, lo + a8, cnt * (uint32_t)sizeof(S), bar, pol);
+  }
+}
+
+// First k in [lo, hi) whose RowInStrip is >= r (RowInStrip is non-decreasing
+// inside an unsorted strip), or hi.
+__device__ __forceinline__ int lb_ris(const uint32_t *cp, long long base, int lo, int hi, uint32_t r, uint32_t mask) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if ((cp[mid - base] & mask) < r) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Dot product of entries [lo, hi) with x, in storage order, one FMA each.
+template <int DT>
+__device__ __forceinline__ typename Form<DT>::Acc row_dot(const uint32_t *cp, const typename Form<DT>::Stored *vh,
+                                                          const typename Form<DT>::Stored *vl, long long base, int lo,
+                                                          int hi, int bits, const typename Form<DT>::Acc *x) {
+  typedef typename Form<DT>::Acc A;
+  A acc = A(0);
+  int k = lo;
+  for (; k + 4 <= hi; k += 4) {
+    const long long i = k - base;
+    const uint32_t c0 = cp[i], c1 = cp[i + 1], c2 = cp[i + 2], c3 = cp[i + 3];
+    const A x0 = ld_x(x + (c0 >> bits)), x1 = ld_x(x + (c1 >> bits)), x2 = ld_x(x + (c2 >> bits)),
+            x3 = ld_x(x + (c3 >> bits));
+    const A v0 = Form<DT>::value(vh, vl, i), v1 = Form<DT>::value(vh, vl, i + 1), v2 = Form<DT>::value(vh, vl, i + 2),
+            v3 = Form<DT>::value(vh, vl, i + 3);
+    acc = fma_acc(v0, x0, acc);
+    acc = fma_acc(v1, x1, acc);
+    acc = fma_acc(v2, x2, acc);
+    acc = fma_acc(v3, x3, acc);
+  }
+  for (; k < hi; ++k) {
+    const long long i = k - base;
+    const uint32_t c = cp[i];
+    acc = fma_acc(Form<DT>::value(vh, vl, i), ld_x(x + (c >> bits)), acc);
+  }
+  return acc;
+}
+
+// ============================================================== ROW mapping
+// CTA b owns rows [128 b, 128 b + 128): the strips holding them are one
+// contiguous range of the nonzero streams, staged by bulk copies two blocks
+// ahead.  Thread t walks row 128 b + t: its bounds inside the strip come from
+// two binary searches on RowInStrip, then one FMA per entry.  A block whose
+// strips exceed the stage capacity is read from global memory instead.
+template <int DT>
+__global__ void __launch_bounds__(kRowThreads) k_spmv_row(int rows, int height, int bits, int nnz,
+                                                          const int32_t *__restrict__ sp,
+                                                          const uint32_t *__restrict__ packed,
+                                                          const typename Form<DT>::Stored *__restrict__ hi,
+                                                          const typename Form<DT>::Stored *__restrict__ lo,
+                                                          const typename Form<DT>::Acc *__restrict__ x,
+                                                          typename Form<DT>::Acc *__restrict__ y, uint32_t *status) {
+  typedef typename Form<DT>::Stored S;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ uint64_t bars[kStages];
+  __shared__ StageInfo info[kStages];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const int nblk = (rows + kRowThreads - 1) / kRowThreads;
+  const uint32_t mask = (1u << bits) - 1;
+  const size_t stage_bytes = Stage<DT>::bytes(kRowCap);
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  uint64_t pol = 0;
+  if (tid == 0) pol = policy_evict_first();
+
+  auto issue = [&](int b, int st) {
+    const long long r0 = (long long)b * kRowThreads;
+    const long long r1 = min(r0 + kRowThreads, (long long)rows);
+    const int s0 = (int)(r0 / height), s1 = (int)((r1 - 1) / height);
+    const long long ea = sp[s0], eb = sp[s1 + 1];
+    if (eb - ea <= kRowCap) {
+      issue_stage<DT>(ea, eb, nnz, packed, hi, lo, smem + st * stage_bytes, kRowCap, &bars[st], pol, &info[st]);
+    } else {
+      info[st].staged = 0;
+      info[st].a8 = 0;
+      mbar_arrive_expect_tx(&bars[st], 0);
+    }
+  };
+
+  int b = blockIdx.x;
+  if (tid == 0 && b < nblk) issue(b, 0);
+  for (int it = 0; b < nblk; ++it, b += gridDim.x) {
+    const int st = it & 1;
+    if (tid == 0 && b + (int)gridDim.x < nblk) issue(b + gridDim.x, st ^ 1);
+    if (!mbar_wait_bounded(&bars[st], (it >> 1) & 1)) {
+      s_abort = 1;
+      atomicOr(status, ST_TIMEOUT);
+    } else {
+      const long long row = (long long)b * kRowThreads + tid;
+      if (row < rows) {
+        const int s = (int)(row / height);
+        const uint32_t r = (uint32_t)(row - (long long)s * height);
+        const int sa = sp[s], sb = sp[s + 1];
+        typename Form<DT>::Acc acc;
+        if (info[st].staged) {
+          const char *stg = smem + st * stage_bytes;
+          const uint32_t *cp = reinterpret_cast<const uint32_t *>(stg);
+          const S *vh = reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kRowCap));
+          const S *vl = reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kRowCap) + Stage<DT>::val_bytes(kRowCap));
+          const long long base = info[st].a8;
+          int k0 = sa, k1 = sb;
+          if (height > 1) {
+            k0 = lb_ris(cp, base, sa, sb, r, mask);
+            k1 = lb_ris(cp, base, k0, sb, r + 1, mask);
+          }
+          acc = row_dot<DT>(cp, vh, vl, base, k0, k1, bits, x);
+        } else {
+          const S *vl = Stage<DT>::kSplit ? lo : hi;
+          int k0 = sa, k1 = sb;
+          if (height > 1) {
+            k0 = lb_ris(packed, 0, sa, sb, r, mask);
+            k1 = lb_ris(packed, 0, k0, sb, r + 1, mask);
+          }
+          acc = row_dot<DT>(packed, hi, vl, 0, k0, k1, bits, x);
+        }
+        y[row] = acc;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+  }
+}
+
+// ============================================================== STRIP mapping
+// Algorithm 1 of Section 4: one warp per strip, lane l takes entries
+// strip_start + l, + 32, ...; each entry's product is added to buf[r][l] (r =
+// RowInStrip); the 32 partial sums of every row are then halved five times
+// (l += l + 16, 8, 4, 2, 1) and lanes < height write the rows.  The buffer is
+// laid out row-major [r][32] so that the lanes of a warp touch 32 banks.
+template <int DT>
+__global__ void __launch_bounds__(kStripWarps * 32) k_spmv_strip(int rows, int height, int bits, int strips,
+                                                                  const int32_t *__restrict__ sp,
+                                                                  const uint32_t *__restrict__ packed,
+                                                                  const typename Form<DT>::Stored *__restrict__ hi,
+                                                                  const typename Form<DT>::Stored *__restrict__ lo,
+                                                                  const typename Form<DT>::Acc *__restrict__ x,
+                                                                  typename Form<DT>::Acc *__restrict__ y) {
+  typedef typename Form<DT>::Acc A;
+  extern __shared__ __align__(128) char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  A *buf = reinterpret_cast<A *>(smem) + (size_t)w * height * 32;
+  const uint32_t mask = (1u << bits) - 1;
+  const int nw = gridDim.x * kStripWarps;
+  const typename Form<DT>::Stored *vl = Stage<DT>::kSplit ? lo : hi;
+  for (int s = blockIdx.x * kStripWarps + w; s < strips; s += nw) {
+    for (int r = 0; r < height; ++r) buf[r * 32 + lane] = A(0);
+    const int a = sp[s], b = sp[s + 1];
+    for (int j = a + lane; j < b; j += 32) {
+      const uint32_t c = packed[j];
+      const int r = (int)(c & mask);
+      if (r < height) {
+        A *p = buf + r * 32 + lane;
+        *p = fma_acc(Form<DT>::value(hi, vl, j), ld_x(x + (c >> bits)), *p);
+      }
+    }
+    __syncwarp();
+    for (int half = 16; half >= 1; half >>= 1) {
+      for (int idx = lane; idx < height * half; idx += 32) {
+        const int r = idx / half, l = idx - r * half;
+        buf[r * 32 + l] += buf[r * 32 + l + half];
+      }
+      __syncwarp();
+    }
+    if (lane < height) {
+      const long long row = (long long)s * height + lane;
+      if (row < rows) y[row] = buf[lane * 32];
+    }
+    __syncwarp();
+  }
+}
+
+// ============================================================== MERGE mapping
+// Tile t = entries [1920 t, 1920 t + 1920), staged by bulk copies; thread i
+// owns the 15 consecutive entries from 1920 t + 15 i.  It finds their strip by
+// a binary search of StripPtr between the strips holding the tile's first
+// and next tile's first entry (tile_strip[], one small pre-pass), then walks
+// the entries: a row's run is summed by one FMA chain; a run that starts and
+// ends inside the thread is written at once; a run cut by the thread's end is
+// joined, after a CTA barrier, by the thread where it started (walking over
+// the following threads' head partials in order); a run cut by the tile's end
+// goes to a tile record that a fix-up kernel joins in tile order.  Rows with
+// no entries are written as 0 by the thread owning the entry before the gap.
+__global__ void k_tile_map(int strips, const int32_t *__restrict__ sp, int ntiles, int32_t *__restrict__ tile_strip) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= strips) return;
+  const long long a = sp[s], b = sp[s + 1];
+  if (b <= a) return;
+  for (long long t = (a + kMergeTile - 1) / kMergeTile; t * kMergeTile < b && t < ntiles; ++t) tile_strip[t] = s;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kMergeThreads) k_spmv_merge(int rows, int height, int bits, int strips, int nnz,
+                                                              const int32_t *__restrict__ sp,
+                                                              const uint32_t *__restrict__ packed,
+                                                              const typename Form<DT>::Stored *__restrict__ hi,
+                                                              const typename Form<DT>::Stored *__restrict__ lo,
+                                                              const typename Form<DT>::Acc *__restrict__ x,
+                                                              typename Form<DT>::Acc *__restrict__ y,
+                                                              const int32_t *__restrict__ tile_strip, int ntiles,
+                                                              TileRec *__restrict__ recs, uint32_t *status) {
+  typedef typename Form<DT>::Stored S;
+  typedef typename Form<DT>::Acc A;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ uint64_t bars[kStages];
+  __shared__ StageInfo info[kStages];
+  __shared__ A s_head[kMergeThreads], s_tail[kMergeThreads];
+  __shared__ int s_hrow[kMergeThreads], s_trow[kMergeThreads];
+  __shared__ uint8_t s_flag[kMergeThreads];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const uint32_t mask = (1u << bits) - 1;
+  const size_t stage_bytes = Stage<DT>::bytes(kMergeTile);
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  uint64_t pol = 0;
+  if (tid == 0) pol = policy_evict_first();
+  auto issue = [&](int t, int st) {
+    const long long ta = (long long)t * kMergeTile;
+    const long long tb = min(ta + kMergeTile, (long long)nnz);
+    issue_stage<DT>(ta, tb, nnz, packed, hi, lo, smem + st * stage_bytes, kMergeTile, &bars[st], pol, &info[st]);
+  };
+  int t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t, 0);
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const int st = it & 1;
+    if (tid == 0) {
+      if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x, st ^ 1);
+      recs[t].tail_flag = 0;
+    }
+    const bool ok = mbar_wait_bounded(&bars[st], (it >> 1) & 1);
+    if (!ok) {
+      s_abort = 1;
+      atomicOr(status, ST_TIMEOUT);
+    }
+    const char *stg = smem + st * stage_bytes;
+    const uint32_t *cp = reinterpret_cast<const uint32_t *>(stg);
+    const S *vh = reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kMergeTile));
+    const S *vl = reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kMergeTile) + Stage<DT>::val_bytes(kMergeTile));
+    const long long base = info[st].a8;
+    const long long ta = (long long)t * kMergeTile;
+    const long long tb = min(ta + kMergeTile, (long long)nnz);
+    const long long k0 = ta + (long long)tid * kMergeE;
+    const long long k1 = min(k0 + kMergeE, tb);
+    uint8_t flags = 0;
+    if (ok && k0 < tb) {
+      // strip holding k0: the largest s in [s_lo, s_hi] with StripPtr[s] <= k0
+      int slo = tile_strip[t];
+      int shi = (t + 1 < ntiles) ? tile_strip[t + 1] : strips - 1;
+      while (slo < shi) {
+        const int mid = (slo + shi + 1) >> 1;
+        if (sp[mid] <= k0) slo = mid;
+        else shi = mid - 1;
+      }
+      int cur = slo;
+      long long next = sp[cur + 1];
+      // does the entry before k0 (previous thread, or previous tile for thread 0) lie in the same row?
+      bool cont_in = false;
+      if (k0 > sp[cur]) {
+        const uint32_t cprev = k0 > ta ? cp[k0 - 1 - base] : __ldg(packed + k0 - 1);
+        cont_in = (cprev & mask) == (cp[k0 - base] & mask);
+      }
+      // operands first, so that the x loads of the run are in flight together
+      uint32_t c[kMergeE];
+      A xv[kMergeE], v[kMergeE];
+#pragma unroll
+      for (int j = 0; j < kMergeE; ++j) {
+        if (k0 + j < k1) {
+          const long long i = k0 + j - base;
+          c[j] = cp[i];
+          v[j] = Form<DT>::value(vh, vl, i);
+          xv[j] = ld_x(x + (c[j] >> bits));
+        }
+      }
+      long long run_row = -1;
+      A acc = A(0), head_sum = A(0);
+      int nruns = 0;
+      long long head_row = -1;
+      if (k0 == 0) {
+        // rows before the first entry of the matrix are empty
+        while (k0 >= next) next = sp[++cur + 1];
+        const long long r0 = (long long)cur * height + (c[0] & mask);
+        for (long long g = 0; g < r0 && g < rows; ++g) y[g] = A(0);
+      }
+#pragma unroll
+      for (int j = 0; j < kMergeE; ++j) {
+        if (k0 + j < k1) {
+          const long long k = k0 + j;
+          while (k >= next) next = sp[++cur + 1];
+          const long long row = (long long)cur * height + (c[j] & mask);
+          if (row != run_row) {
+            if (run_row >= 0) {
+              if (nruns == 1 && cont_in) {
+                head_sum = acc;
+                head_row = run_row;
+              } else if (run_row < rows) {
+                y[run_row] = acc;
+              }
+              for (long long g = run_row + 1; g < row && g < rows; ++g) y[g] = A(0);
+            }
+            run_row = row;
+            acc = A(0);
+            ++nruns;
+          }
+          acc = fma_acc(v[j], xv[j], acc);
+        }
+      }
+      // the entry after this thread's last one: same row?
+      long long next_row = rows;
+      if (k1 < nnz) {
+        const uint32_t cn = (k1 < tb) ? cp[k1 - base] : __ldg(packed + k1);
+        int s2 = cur;
+        while (k1 >= sp[s2 + 1]) ++s2;
+        next_row = (long long)s2 * height + (cn & mask);
+      }
+      const bool cont_out = next_row == run_row;
+      if (nruns == 1 && cont_in) {
+        s_head[tid] = acc;
+        s_hrow[tid] = (int)run_row;
+        flags = cont_out ? (F_HEAD | F_THROUGH) : F_HEAD;
+      } else {
+        if (head_row >= 0) {
+          s_head[tid] = head_sum;
+          s_hrow[tid] = (int)head_row;
+          flags = F_HEAD;
+        }
+        if (cont_out) {
+          s_tail[tid] = acc;
+          s_trow[tid] = (int)run_row;
+          flags |= F_TAIL;
+        } else if (run_row < rows) {
+          y[run_row] = acc;
+        }
+      }
+      if (!cont_out)
+        for (long long g = run_row + 1; g < next_row && g < rows; ++g) y[g] = A(0);
+    }
+    s_flag[tid] = flags;
+    __syncthreads();
+    if (!s_abort) {
+      if ((flags & F_TAIL) && !(flags & F_THROUGH)) {
+        A sum = s_tail[tid];
+        const int row = s_trow[tid];
+        int j = tid + 1;
+        for (;;) {
+          if (j >= kMergeThreads) {
+            recs[t].tail_row = row;
+            recs[t].tail_sum = (double)sum;
+            recs[t].tail_flag = 1;
+            break;
+          }
+          sum += s_head[j];
+          if (s_flag[j] & F_THROUGH) {
+            ++j;
+            continue;
+          }
+          if (row < rows) y[row] = sum;
+          break;
+        }
+      }
+      if (tid == 0) {
+        if (flags & F_HEAD) {
+          A sum = s_head[0];
+          int j = 0;
+          while ((s_flag[j] & F_THROUGH) && j + 1 < kMergeThreads) {
+            ++j;
+            sum += s_head[j];
+          }
+          recs[t].head_row = s_hrow[0];
+          recs[t].head_sum = (double)sum;
+          recs[t].head_flag = (s_flag[j] & F_THROUGH) ? 2 : 1;
+        } else {
+          recs[t].head_flag = 0;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+  }
+}
+
+template <typename A>
+__global__ void k_merge_fixup(int ntiles, int rows, const TileRec *__restrict__ recs, A *__restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles || recs[t].tail_flag != 1) return;
+  A sum = (A)recs[t].tail_sum;
+  for (int u = t + 1; u < ntiles; ++u) {
+    sum += (A)recs[u].head_sum;
+    if (recs[u].head_flag != 2) break;
+  }
+  if (recs[t].tail_row < rows) y[recs[t].tail_row] = sum;
+}
+
+// ============================================================== host side
+struct Occ {
+  std::mutex mu;
+  int val[64] = {0};
+};
+
+template <typename K>
+int occupancy(K kernel, int threads, size_t smem, Occ &cache) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lk(cache.mu);
+  if (cache.val[dev] == 0) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    cache.val[dev] = n;
+  }
+  return cache.val[dev];
+}
+
+size_t merge_ws_bytes(int nnz) {
+  const long long ntiles = ceil_div(nnz, kMergeTile);
+  return 256 + align256((size_t)(ntiles + 1) * 4) + align256((size_t)ntiles * sizeof(TileRec));
+}
+
+template <int DT>
+int launch(const cmrs_matrix *A, const void *xv, void *yv, int variant, char *ws, cudaStream_t st) {
+  typedef typename Form<DT>::Stored S;
+  typedef typename Form<DT>::Acc Acc;
+  const S *hi = reinterpret_cast<const S *>(A->val);
+  const S *lo = DT == CMRS_BF16X2 ? hi + cmrs_pad8(A->nnz) : nullptr;
+  const Acc *x = reinterpret_cast<const Acc *>(xv);
+  Acc *y = reinterpret_cast<Acc *>(yv);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+  const int sms = sm_count();
+  if (variant == CMRS_VARIANT_ROW) {
+    static Occ occ;
+    const size_t smem = kStages * Stage<DT>::bytes(kRowCap);
+    const int per_sm = occupancy(k_spmv_row<DT>, kRowThreads, smem, occ);
+    const long long nblk = ceil_div(A->rows, kRowThreads);
+    const int grid = (int)std::min<long long>(nblk, (long long)per_sm * sms);
+    k_spmv_row<DT><<<grid, kRowThreads, smem, st>>>(A->rows, A->height, A->bits, A->nnz, A->strip_ptr, A->col_packed,
+                                                    hi, lo, x, y, status);
+    CMRS_LAUNCH_CHECK();
+  } else if (variant == CMRS_VARIANT_STRIP) {
+    static Occ occ;
+    const size_t smem = (size_t)kStripWarps * A->height * 32 * sizeof(Acc);
+    const int per_sm = occupancy(k_spmv_strip<DT>, kStripWarps * 32, (size_t)kStripWarps * 32 * 32 * sizeof(Acc), occ);
+    const long long need = ceil_div(A->strips, kStripWarps);
+    const int grid = (int)std::min<long long>(need, (long long)per_sm * sms);
+    k_spmv_strip<DT><<<grid, kStripWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->strip_ptr,
+                                                           A->col_packed, hi, lo, x, y);
+    CMRS_LAUNCH_CHECK();
+  } else {
+    static Occ occ;
+    const int ntiles = (int)ceil_div(A->nnz, kMergeTile);
+    int32_t *tile_strip = reinterpret_cast<int32_t *>(ws + 256);
+    TileRec *recs = reinterpret_cast<TileRec *>(ws + 256 + align256((size_t)(ntiles + 1) * 4));
+    k_tile_map<<<(int)ceil_div(A->strips, 256), 256, 0, st>>>(A->strips, A->strip_ptr, ntiles, tile_strip);
+    CMRS_LAUNCH_CHECK();
+    const size_t smem = kStages * Stage<DT>::bytes(kMergeTile);
+    const int per_sm = occupancy(k_spmv_merge<DT>, kMergeThreads, smem, occ);
+    const int grid = (int)std::min<long long>(ntiles, (long long)per_sm * sms);
+    k_spmv_merge<DT><<<grid, kMergeThreads, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->nnz, A->strip_ptr,
+                                                        A->col_packed, hi, lo, x, y, tile_strip, ntiles, recs, status);
+    CMRS_LAUNCH_CHECK();
+    k_merge_fixup<Acc><<<(int)ceil_div(ntiles, 256), 256, 0, st>>>(ntiles, A->rows, recs, y);
+    CMRS_LAUNCH_CHECK();
+  }
+  return CMRS_OK;
+}
+
+int check_matrix(const cmrs_matrix *A) {
+  if (!A) return CMRS_ERR_ARG;
+  if (A->rows < 0 || A->cols < 0 || A->nnz < 0) return CMRS_ERR_ARG;
+  if (cmrs_bits_for_height(A->height) < 0) return CMRS_ERR_HEIGHT;
+  if (A->bits != cmrs_bits_for_height(A->height)) return CMRS_ERR_ARG;
+  if (A->strips != ceil_div(A->rows, A->height)) return CMRS_ERR_ARG;
+  if (A->dtype < CMRS_F64 || A->dtype > CMRS_BF16X2) return CMRS_ERR_ARG;
+  if (A->flags & ~CMRS_SORTED) return CMRS_ERR_ARG;
+  if (A->rows > 0 && !A->strip_ptr) return CMRS_ERR_ARG;
+  if (A->nnz > 0 && (!A->col_packed || !A->val)) return CMRS_ERR_ARG;
+  return CMRS_OK;
+}
+
+int resolve_variant(const cmrs_matrix *A, int variant, int *out) {
+  const bool sorted = (A->flags & CMRS_SORTED) != 0;
+  if (variant == CMRS_VARIANT_AUTO) variant = sorted ? CMRS_VARIANT_STRIP : CMRS_VARIANT_ROW;
+  if (variant < 0 || variant >= CMRS_NUM_VARIANTS) return CMRS_ERR_ARG;
+  if (sorted && variant != CMRS_VARIANT_STRIP) return CMRS_ERR_UNSUPPORTED;
+  *out = variant;
+  return CMRS_OK;
+}
+
+}  // namespace
+}  // namespace cmrs
+
+using namespace cmrs;
+
+extern "C" int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes) {
+  if (!bytes) return CMRS_ERR_ARG;
+  int rc = check_matrix(A);
+  if (rc) return rc;
+  int v = 0;
+  rc = resolve_variant(A, variant, &v);
+  if (rc) return rc;
+  *bytes = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz) : 256;
+  return CMRS_OK;
+}
+
+extern "C" int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant, void *workspace,
+                         size_t workspace_bytes, void *stream) {
+  int rc = check_matrix(A);
+  if (rc) return rc;
+  int v = 0;
+  rc = resolve_variant(A, variant, &v);
+  if (rc) return rc;
+  if (A->rows == 0) return CMRS_OK;
+  if (!y || (A->nnz > 0 && !x)) return CMRS_ERR_ARG;
+  const size_t need = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz) : 256;
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CMRS_ERR_WORKSPACE;
+  // ROW and MERGE stream col_packed and val with bulk copies: 16-byte aligned bases
+  if (v != CMRS_VARIANT_STRIP && A->nnz > 0 &&
+      ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(A->val)) & 15))
+    return CMRS_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  const size_t ysz = A->dtype == CMRS_F64 ? 8 : 4;
+  if (A->nnz == 0) {
+    CMRS_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)A->rows * ysz, st));
+    return CMRS_OK;
+  }
+  char *ws = reinterpret_cast<char *>(workspace);
+  switch (A->dtype) {
+    case CMRS_F64: return launch<CMRS_F64>(A, x, y, v, ws, st);
+    case CMRS_F32: return launch<CMRS_F32>(A, x, y, v, ws, st);
+    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, v, ws, st);
+    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, v, ws, st);
+  }
+  return CMRS_ERR_ARG;
+}
+
+extern "C" int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, void *stream) {
+  (void)A;
+  (void)variant;
+  if (!workspace) return CMRS_ERR_ARG;
+  uint32_t s = 0;
+  cudaStream_t st = as_stream(stream);
+  CMRS_CUDA_TRY(cudaMemcpyAsync(&s, workspace, 4, cudaMemcpyDeviceToHost, st));
+  CMRS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (s & ST_TIMEOUT) {
+    CMRS_CUDA_TRY(cudaMemsetAsync(const_cast<void *>(workspace), 0, 4, st));
+    return CMRS_ERR_TIMEOUT;
+  }
+  return CMRS_OK;
+}

@@ -1,0 +1,308 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Bars: conversions and every index array bit-exact; stored values bit-exact
+against the oracle's encoders; FP64 SpMV |y - y*| <= 1e-12 * (|A||x|)_i
+(exactly 0 where that scale is 0); FP32-accumulated forms within
+(len_i + 2) * 2^-24 * (|A_q||x_q|)_i of the quantised-input oracle (values as
+stored, x as FP32, FP64 sums), which bounds any summation order of len_i
+exact products in FP32."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1203_2946_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = [0, 1, 2, 3]
+VARIANTS = [0, 1, 2]
+
+
+@pytest.fixture(scope="module")
+def b():
+    from paper_1203_2946_gb300 import build
+    build.build()
+    from paper_1203_2946_gb300 import binding
+    assert torch.cuda.is_available()
+    return binding
+
+
+def dev(a):
+    return (torch.from_numpy(a.row_ptr).cuda(), torch.from_numpy(a.col_ind).cuda(),
+            torch.from_numpy(np.ascontiguousarray(a.val)).cuda())
+
+
+def stored_np(b, M):
+    t = b.stored_values(M).cpu().numpy()
+    return t.view(np.uint16) if t.dtype == np.int16 else t
+
+
+def convert(b, a, h, sorted_=False, dtype=0):
+    rp, ci, v = dev(a)
+    M = b.cmrs_from_csr(rp, ci, v, a.cols, h, flags=1 if sorted_ else 0, dtype=dtype)
+    torch.cuda.synchronize()
+    return M
+
+
+def check_conversion(b, a, h, sorted_=False, dtype=0):
+    M = convert(b, a, h, sorted_, dtype)
+    ref = orc.csr_to_cmrs(a.row_ptr, a.col_ind, a.val.astype(np.float64), a.cols, h, sorted_)
+    assert np.array_equal(M.strip_ptr.cpu().numpy(), ref["strip_ptr"])
+    assert np.array_equal(M.col_packed.cpu().numpy()[:a.nnz].view(np.uint32), ref["packed"])
+    assert np.array_equal(stored_np(b, M), orc.encode(a.val[ref["src"]], dtype))
+    lens = np.diff(ref["strip_ptr"])
+    assert M.struct.max_strip_nnz == (int(lens.max()) if lens.size else 0)
+    return M
+
+
+def xvec(a, dtype, seed=5):
+    x = np.random.default_rng(seed).uniform(-1, 1, a.cols)
+    return x if dtype == 0 else x.astype(np.float32)
+
+
+def check_spmv(b, M, a, x, variant, dtype):
+    y = b.cmrs_spmv(M, torch.from_numpy(x).cuda(), variant=variant).cpu().numpy()
+    assert y.shape == (a.rows,)
+    if dtype == 0:
+        yref, absy = orc.csr_spmv(a.row_ptr, a.col_ind, a.val.astype(np.float64), x)
+        err = np.abs(y - yref)
+        bad = err > 1e-12 * absy
+        assert not bad.any(), (variant, np.nonzero(bad)[0][:10], err[bad][:5], absy[bad][:5])
+        return err
+    vq = orc.decode(orc.encode(a.val, dtype), dtype, a.nnz)
+    yq, aq = orc.csr_spmv(a.row_ptr, a.col_ind, vq, x.astype(np.float64))
+    L = np.diff(a.row_ptr)
+    tol = (L + 2) * 2.0**-24 * aq
+    err = np.abs(y.astype(np.float64) - yq)
+    bad = err > tol
+    assert not bad.any(), (variant, dtype, np.nonzero(bad)[0][:10], err[bad][:5], tol[bad][:5])
+    return err
+
+
+# ------------------------------------------------------------------ the paper's worked example
+def test_golden_5x5(b, golden5):
+    rp, ci, v = (golden5["crs_rowptr"].astype(np.int32), golden5["crs_colind"].astype(np.int32), golden5["crs_val"])
+    a = inputs.CSR(5, 5, rp, ci, v)
+    M = convert(b, a, 2)
+    assert np.array_equal(M.strip_ptr.cpu().numpy(), golden5["cmrs_h2_stripptr"])
+    pk = M.col_packed.cpu().numpy()[:10].view(np.uint32)
+    assert np.array_equal(pk >> 4, golden5["cmrs_h2_colind"]) and np.array_equal(pk & 15, golden5["cmrs_h2_rowinstrip"])
+    S = convert(b, a, 2, sorted_=True)
+    pk = S.col_packed.cpu().numpy()[:10].view(np.uint32)
+    assert np.array_equal(pk >> 4, golden5["sorted_h2_colind"])
+    assert np.array_equal(pk & 15, golden5["sorted_h2_rowinstrip"])
+    assert np.array_equal(stored_np(b, S), golden5["sorted_h2_val"])
+    ones = torch.ones(5, dtype=torch.float64, device="cuda")
+    for var in VARIANTS:
+        assert b.cmrs_spmv(M, ones, variant=var).cpu().numpy().tolist() == [3, 7, 11, 24, 10]
+    assert b.cmrs_spmv(S, ones, variant=1).cpu().numpy().tolist() == [3, 7, 11, 24, 10]
+    for sorted_ in (0, 1):
+        X = convert(b, a, 2, sorted_=bool(sorted_))
+        rp2, ci2, vo = b.cmrs_to_csr(X)
+        assert np.array_equal(rp2.cpu().numpy(), rp) and np.array_equal(ci2.cpu().numpy(), ci)
+        assert np.array_equal(vo.view(torch.float64)[:10].cpu().numpy(), v)
+
+
+# ------------------------------------------------------------------ conversions
+@pytest.mark.parametrize("h", [1, 2, 3, 4, 5, 8, 16, 17, 32])
+@pytest.mark.parametrize("sorted_", [False, True])
+def test_conversion_bit_exact(b, h, sorted_):
+    a = inputs.random_csr(1500, 900, 0.01, seed=h, empty_row_frac=0.2)
+    for dtype in DTYPES:
+        check_conversion(b, a, h, sorted_, dtype)
+
+
+def test_conversion_f32_input_forms(b):
+    a = inputs.powerlaw_rows(30000, 2.1, 3000, seed=2)
+    for h in (1, 4, 32):
+        for dtype in DTYPES:
+            check_conversion(b, a, h, False, dtype)
+        check_conversion(b, a, h, True, 1)
+
+
+@pytest.mark.parametrize("h", [1, 4, 8, 32])
+def test_round_trip(b, h):
+    a = inputs.random_csr(3001, 700, 0.02, seed=40 + h, empty_row_frac=0.3)
+    for sorted_ in (False, True):
+        for dtype in DTYPES:
+            M = convert(b, a, h, sorted_, dtype)
+            rp, ci, vo = b.cmrs_to_csr(M)
+            assert np.array_equal(rp.cpu().numpy(), a.row_ptr)
+            assert np.array_equal(ci.cpu().numpy(), a.col_ind)
+            nb = b.lib().cmrs_val_bytes(a.nnz, dtype)
+            ref = orc.encode(a.val, dtype)
+            got = vo.cpu().numpy()
+            if dtype == 3:
+                pad = b.lib().cmrs_pad8(a.nnz)
+                got16 = got.view(np.uint16)
+                got = np.concatenate([got16[:a.nnz], got16[pad:pad + a.nnz]])
+            else:
+                got = got[:nb].view(ref.dtype)
+            assert np.array_equal(got, ref)
+
+
+def test_long_strips_sort_and_round_trip(b):
+    # one 9000-entry row and one 2500-entry row put strips past the 1024-entry
+    # shared-memory sort into the radix path
+    L = np.full(3000, 3)
+    L[7] = 9000
+    L[2050] = 2500
+    L[100:130] = 0
+    a = inputs.from_lengths(L, 20000, seed=3)
+    for h in (4, 32):
+        for dtype in (0, 3):
+            M = check_conversion(b, a, h, True, dtype)
+            rp, ci, _ = b.cmrs_to_csr(M)
+            assert np.array_equal(rp.cpu().numpy(), a.row_ptr) and np.array_equal(ci.cpu().numpy(), a.col_ind)
+
+
+def test_invalid_csr_reported(b):
+    a = inputs.random_csr(50, 50, 0.1, seed=1)
+    rp, ci, v = dev(a)
+    bad = ci.clone()
+    bad[3] = 50
+    with pytest.raises(b.CmrsError) as e:
+        b.cmrs_from_csr(rp, bad, v, 50, 4)
+    assert e.value.code == 4
+    rpb = rp.clone()
+    rpb[10] = rpb[11] + 1
+    with pytest.raises(b.CmrsError) as e:
+        b.cmrs_from_csr(rpb, ci, v, 50, 4)
+    assert e.value.code == 4
+    rpb = rp.clone()
+    rpb[-1] = rpb[-1] - 1
+    with pytest.raises(b.CmrsError) as e:
+        b.cmrs_from_csr(rpb, ci, v, 50, 4)
+    assert e.value.code == 4
+    with pytest.raises(b.CmrsError) as e:
+        b.cmrs_from_csr(rp, ci, v, 50, 33)
+    assert e.value.code == 2
+
+
+# ------------------------------------------------------------------ SpMV
+@pytest.mark.parametrize("h", [1, 2, 3, 4, 8, 16, 32])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_spmv_random(b, h, dtype):
+    a = inputs.random_csr(6007, 5000, 0.004, seed=h + 10 * dtype, empty_row_frac=0.1)
+    M = convert(b, a, h, False, dtype)
+    x = xvec(a, dtype)
+    for var in VARIANTS:
+        check_spmv(b, M, a, x, var, dtype)
+    S = convert(b, a, h, True, dtype)
+    check_spmv(b, S, a, x, 1, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_spmv_skewed_rows(b, dtype):
+    # rows longer than a MERGE tile (1920) and a ROW stage (4096), empty rows,
+    # empty strips, a ragged tail strip
+    L = np.random.default_rng(1).integers(0, 12, 20001)
+    L[5] = 7000
+    L[777] = 1930
+    L[778] = 1919
+    L[5000:5400] = 0
+    L[-1] = 2
+    a = inputs.from_lengths(L, 30000, seed=9, dtype=np.float64)
+    x = xvec(a, dtype)
+    for h in (1, 4, 7, 32):
+        M = convert(b, a, h, False, dtype)
+        for var in VARIANTS:
+            check_spmv(b, M, a, x, var, dtype)
+
+
+def test_spmv_degenerate(b):
+    # nnz = 0 with rows > 0: y = 0
+    a = inputs.from_lengths(np.zeros(100, int), 10, seed=1)
+    for var in VARIANTS:
+        M = convert(b, a, 4)
+        y = b.cmrs_spmv(M, torch.ones(10, dtype=torch.float64, device="cuda"), variant=var)
+        assert (y == 0).all()
+    # one row holding every entry, at the end; everything before it empty
+    L = np.zeros(333, int)
+    L[-1] = 5000
+    a = inputs.from_lengths(L, 6000, seed=2)
+    for h in (1, 4, 32):
+        M = convert(b, a, h)
+        for var in VARIANTS:
+            check_spmv(b, M, a, xvec(a, 0), var, 0)
+    # a single entry at the very first row; identity; diagonal
+    a = inputs.from_lengths(np.array([1] + [0] * 50), 3, seed=3)
+    M = convert(b, a, 4)
+    for var in VARIANTS:
+        check_spmv(b, M, a, xvec(a, 0), var, 0)
+    n = 10007
+    ident = inputs.CSR(n, n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    x = xvec(ident, 0)
+    for h in (1, 3, 32):
+        M = convert(b, ident, h)
+        for var in VARIANTS:
+            assert np.array_equal(b.cmrs_spmv(M, torch.from_numpy(x).cuda(), variant=var).cpu().numpy(), x)
+    # rows = 0
+    a = inputs.CSR(0, 5, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    M = convert(b, a, 4)
+    assert b.cmrs_spmv(M, torch.ones(5, dtype=torch.float64, device="cuda")).numel() == 0
+
+
+def test_spmv_repeatable(b):
+    a = inputs.powerlaw_rows(50000, 2.1, 20000, seed=4)
+    x = xvec(a, 1)
+    xs = torch.from_numpy(x).cuda()
+    for h in (4, 16):
+        M = convert(b, a, h, False, 1)
+        for var in VARIANTS:
+            y1 = b.cmrs_spmv(M, xs, variant=var)
+            y2 = b.cmrs_spmv(M, xs, variant=var)
+            assert torch.equal(y1, y2)
+            b.cmrs_spmv_check(M, var)
+
+
+def test_laplacian_64_config(b):
+    """5-point Laplacian 64x64, FP64, h = 4: conversion + SpMV against the oracle."""
+    a, x = inputs.workload_laplacian_64()
+    M = check_conversion(b, a, 4)
+    for var in VARIANTS:
+        check_spmv(b, M, a, x, var, 0)
+    ones = torch.ones(a.cols, dtype=torch.float64, device="cuda")
+    g = b.cmrs_spmv(M, ones).cpu().numpy().reshape(64, 64)
+    assert (g[1:-1, 1:-1] == 0).all() and g[0, 0] == 2 and g[0, 5] == 1
+
+
+# ------------------------------------------------------------------ full-size workloads
+@pytest.fixture(scope="module")
+def stencil27():
+    return inputs.workload_stencil27_128()
+
+
+@pytest.mark.parametrize("h", [4, 16, 32])
+def test_stencil27_full_fp64(b, stencil27, h):
+    a, x = stencil27
+    assert a.nnz == 55_742_968
+    M = check_conversion(b, a, h)
+    for var in VARIANTS:
+        check_spmv(b, M, a, x, var, 0)
+
+
+def test_stencil27_full_reduced(b, stencil27):
+    a, x = stencil27
+    for dtype in (1, 2, 3):
+        M = convert(b, a, 4, False, dtype)
+        check_spmv(b, M, a, x.astype(np.float32), 0, dtype)
+
+
+def test_stencil27_full_sorted(b, stencil27):
+    a, x = stencil27
+    M = check_conversion(b, a, 4, True, 0)
+    check_spmv(b, M, a, x, 1, 0)
+
+
+def test_powerlaw_full(b):
+    a, x = inputs.workload_powerlaw_4m()
+    assert a.rows == 4_194_304
+    for h in (4, 32):
+        M = check_conversion(b, a, h, False, 1)
+        for var in VARIANTS:
+            check_spmv(b, M, a, x, var, 1)
+    M = convert(b, a, 4, False, 2)
+    check_spmv(b, M, a, x, 2, 2)
