@@ -500,7 +500,8 @@ int occupancy(K kernel, int threads, size_t smem, Occ &cache) {
   if (dev < 0 || dev >= 64) dev = 0;
   std::lock_guard<std::mutex> lk(cache.mu);
   if (cache.val[dev] == 0) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // opt in to the dynamic shared memory the launch uses (static + dynamic may pass 48 KB)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
     cache.val[dev] = n;
