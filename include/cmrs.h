@@ -172,6 +172,93 @@ int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant,
  * memory synchronously on `stream`. */
 int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, void *stream);
 
+/* ---- multi right-hand-side SpMM, single and batched ----------------------
+ * Y = A X for CMRS_F32 matrices with unsorted strips; X device [cols][k] and
+ * Y device [rows][k], row-major FP32, FP32 accumulation.  Not in the paper:
+ * the strip layout of Section 3 applied to k right-hand sides at once.
+ * cmrs_spmm: one matrix, one launch, asynchronous. */
+int cmrs_spmm(const cmrs_matrix *A, int k, const float *X, float *Y, void *stream);
+
+/* Batched form: many uneven matrices in one persistent launch.  A plan holds
+ * the schedule -- work units (matrix, row range) of about `work_target`
+ * entry-columns each, heaviest first, fetched by warps from a device queue --
+ * and, with use_graph != 0, a CUDA graph of {queue reset, persistent kernel}.
+ * A[b] (host array of pointers to host structs), k[b], X[b], Y[b] (host
+ * arrays of device pointers) for b < batch.  The plan's device part lives in
+ * `workspace` (>= cmrs_spmm_plan_workspace() bytes, 256-byte aligned), which
+ * must outlive the plan; creation copies the schedule and synchronises
+ * `stream` once.  cmrs_spmm_batched replays the plan on `stream`
+ * (asynchronous).  The plan is a host object released by
+ * cmrs_spmm_plan_destroy. */
+typedef struct cmrs_spmm_plan cmrs_spmm_plan;
+int cmrs_spmm_plan_workspace(int batch, const cmrs_matrix *const *A, const int32_t *k, int work_target,
+                             size_t *bytes);
+int cmrs_spmm_plan_create(int batch, const cmrs_matrix *const *A, const int32_t *k, const float *const *X,
+                          float *const *Y, int work_target, int use_graph, void *workspace,
+                          size_t workspace_bytes, void *stream, cmrs_spmm_plan **plan);
+int cmrs_spmm_batched(cmrs_spmm_plan *plan, void *stream);
+int cmrs_spmm_plan_info(const cmrs_spmm_plan *plan, int *nunits, int *grid, int *work_target);
+int cmrs_spmm_plan_destroy(cmrs_spmm_plan *plan);
+
+/* Autotuner of the batch schedule: times `reps` replays of a graph plan for
+ * each candidate work_target and returns the fastest (best_ms: mean per
+ * replay).  Synchronises `stream`.  workspace as for the largest plan. */
+int cmrs_spmm_autotune(int batch, const cmrs_matrix *const *A, const int32_t *k, const float *const *X,
+                       float *const *Y, const int *candidates, int ncand, int reps, void *workspace,
+                       size_t workspace_bytes, void *stream, int *best_target, float *best_ms);
+
+/* ---- strip selector -------------------------------------------------------
+ * Not in the paper: Section 6.2 chooses the strip height by brute force and
+ * Section 6.7 measures what per-matrix tuning gains.  The selector predicts
+ * (height, variant) from CMRS_NFEAT features of the CRS matrix with a small
+ * MLP (CMRS_NFEAT -> nh -> nh -> CMRS_SEL_CHOICES, ReLU), trained on this
+ * library's own timings by the kernels below.  Choice c means height
+ * {1,2,4,8,16,32}[c / 3] and variant c % 3; the network outputs a predicted
+ * cost per choice and the smallest wins. */
+#define CMRS_NFEAT 24
+#define CMRS_SEL_CHOICES 18
+
+/* Features (device double[CMRS_NFEAT]) of a CRS matrix (device row_ptr,
+ * col_ind), from exact integer sums: log2 rows, log2 nnz, log2(1+mu), row
+ * length CV, log2(1+max row), empty-row fraction, 8 row-length bins,
+ * |col-row| statistics, equal-length neighbour fraction, per-strip column
+ * spread for h = 1..32.  Asynchronous. */
+int cmrs_features_workspace(int rows, size_t *bytes);
+int cmrs_features(int rows, int nnz, const int32_t *row_ptr, const int32_t *col_ind, double *feat,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* Network parameters: one device float array, W1[nh][nin], b1[nh],
+ * W2[nh][nh], b2[nh], W3[nout][nh], b3[nout].  acts (device): Z1, H1, Z2, H2
+ * ([B][nh] each) then O ([B][nout]).  Loss = sum (O - T)^2 / (2 B nout);
+ * grads has the parameter layout; scratch: B * (nout + 2 nh) floats; loss:
+ * device float or NULL.  Adam: the textbook update with bias correction at
+ * 1-based `step`.  All asynchronous. */
+int64_t cmrs_mlp_param_count(int nin, int nh, int nout);
+int cmrs_mlp_forward(int B, int nin, int nh, int nout, const float *X, const float *params, float *acts,
+                     void *stream);
+int cmrs_mlp_backward(int B, int nin, int nh, int nout, const float *X, const float *T, const float *params,
+                      const float *acts, float *grads, float *scratch, float *loss, void *stream);
+int cmrs_mlp_adam(int n, float *params, const float *grads, float *m, float *v, int step, float lr,
+                  float beta1, float beta2, float eps, void *stream);
+
+/* A trained selector (device pointers): input x = (feature - feat_mean) *
+ * feat_scale, nin = CMRS_NFEAT, nout = CMRS_SEL_CHOICES, nh <= 64. */
+typedef struct cmrs_selector {
+  int32_t nin, nh, nout;
+  const float *params;
+  const float *feat_mean;
+  const float *feat_scale;
+} cmrs_selector;
+
+/* Picks (height, variant) for a CRS matrix.  model != NULL: features +
+ * network + argmin on the device.  model == NULL: exhaustive autotune,
+ * converting with every height and timing every variant (5 timed calls
+ * each) on FP32 copies held in the workspace.  Synchronises `stream`. */
+int cmrs_select_strip_workspace(int rows, int cols, int nnz, int exhaustive, size_t *bytes);
+int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row_ptr, const int32_t *col_ind,
+                      const cmrs_selector *model, int *height_out, int *variant_out, void *workspace,
+                      size_t workspace_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

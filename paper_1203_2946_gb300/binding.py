@@ -41,6 +41,15 @@ class cmrs_matrix(ctypes.Structure):
                 ("strip_ptr", ctypes.c_void_p), ("col_packed", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
 
+class cmrs_selector(ctypes.Structure):
+    _fields_ = [("nin", ctypes.c_int32), ("nh", ctypes.c_int32), ("nout", ctypes.c_int32),
+                ("params", ctypes.c_void_p), ("feat_mean", ctypes.c_void_p), ("feat_scale", ctypes.c_void_p)]
+
+
+NFEAT = 24
+SEL_HEIGHTS = (1, 2, 4, 8, 16, 32)
+SEL_CHOICES = 18
+
 _lib = None
 
 
@@ -66,6 +75,24 @@ def lib():
             "cmrs_spmv_workspace": ([M, i, ctypes.POINTER(sz)], i),
             "cmrs_spmv": ([M, vp, vp, i, vp, sz, vp], i),
             "cmrs_spmv_check": ([M, i, vp, vp], i),
+            "cmrs_spmm": ([M, i, vp, vp, vp], i),
+            "cmrs_spmm_plan_workspace": ([i, vp, vp, i, ctypes.POINTER(sz)], i),
+            "cmrs_spmm_plan_create": ([i, vp, vp, vp, vp, i, i, vp, sz, vp, ctypes.POINTER(vp)], i),
+            "cmrs_spmm_batched": ([vp, vp], i),
+            "cmrs_spmm_plan_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
+            "cmrs_spmm_plan_destroy": ([vp], i),
+            "cmrs_spmm_autotune": ([i, vp, vp, vp, vp, vp, i, i, vp, sz, vp, ctypes.POINTER(i),
+                                    ctypes.POINTER(ctypes.c_float)], i),
+            "cmrs_features_workspace": ([i, ctypes.POINTER(sz)], i),
+            "cmrs_features": ([i, i, vp, vp, vp, vp, sz, vp], i),
+            "cmrs_mlp_param_count": ([i, i, i], ctypes.c_int64),
+            "cmrs_mlp_forward": ([i, i, i, i, vp, vp, vp, vp], i),
+            "cmrs_mlp_backward": ([i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp], i),
+            "cmrs_mlp_adam": ([i, vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, vp], i),
+            "cmrs_select_strip_workspace": ([i, i, i, i, ctypes.POINTER(sz)], i),
+            "cmrs_select_strip": ([i, i, i, vp, vp, ctypes.POINTER(cmrs_selector), ctypes.POINTER(i),
+                                   ctypes.POINTER(i), vp, sz, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -211,3 +238,142 @@ def stored_values(A: Matrix):
         w = A.val.view(torch.int16)
         return torch.cat([w[:nnz], w[pad:pad + nnz]])
     return A.val.view(dt)[:nnz]
+
+
+# ----------------------------------------------------------------------------- SpMM
+def cmrs_spmm(A: Matrix, X, Y=None, stream=None):
+    """Y = A X for one CMRS_F32 matrix; X [cols][k] row-major float32."""
+    k = X.shape[1]
+    if Y is None:
+        Y = torch.empty((A.rows, k), dtype=torch.float32, device=X.device)
+    _check(lib().cmrs_spmm(A.ref(), k, _ptr(X), _ptr(Y), _stream(stream)), "cmrs_spmm")
+    return Y
+
+
+def _batch_arrays(mats, Xs, Ys):
+    n = len(mats)
+    A = (ctypes.POINTER(cmrs_matrix) * n)(*[ctypes.pointer(m.struct) for m in mats])
+    k = (ctypes.c_int32 * n)(*[int(X.shape[1]) for X in Xs])
+    Xp = (ctypes.c_void_p * n)(*[X.data_ptr() for X in Xs])
+    Yp = (ctypes.c_void_p * n)(*[Y.data_ptr() for Y in Ys])
+    return A, k, Xp, Yp
+
+
+class SpmmPlan:
+    """A batched SpMM plan: schedule in a device workspace + captured graph."""
+
+    def __init__(self, mats, Xs, Ys, work_target=8192, use_graph=True, stream=None):
+        self._keep = (mats, Xs, Ys)
+        A, k, Xp, Yp = _batch_arrays(mats, Xs, Ys)
+        n = ctypes.c_size_t()
+        _check(lib().cmrs_spmm_plan_workspace(len(mats), A, k, int(work_target), ctypes.byref(n)),
+               "cmrs_spmm_plan_workspace")
+        self.ws = workspace(n.value, Xs[0].device)
+        self.handle = ctypes.c_void_p()
+        _check(lib().cmrs_spmm_plan_create(len(mats), A, k, Xp, Yp, int(work_target), int(bool(use_graph)),
+                                           _ptr(self.ws), n.value, _stream(stream), ctypes.byref(self.handle)),
+               "cmrs_spmm_plan_create")
+
+    def info(self):
+        a, b_, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().cmrs_spmm_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)),
+               "cmrs_spmm_plan_info")
+        return {"units": a.value, "grid": b_.value, "work_target": c.value}
+
+    def close(self):
+        if self.handle:
+            lib().cmrs_spmm_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cmrs_spmm_batched(plan: SpmmPlan, stream=None):
+    _check(lib().cmrs_spmm_batched(plan.handle, _stream(stream)), "cmrs_spmm_batched")
+
+
+def cmrs_spmm_autotune(mats, Xs, Ys, candidates=(1024, 4096, 16384, 65536), reps=5, stream=None):
+    A, k, Xp, Yp = _batch_arrays(mats, Xs, Ys)
+    need = 0
+    for c in candidates:
+        n = ctypes.c_size_t()
+        _check(lib().cmrs_spmm_plan_workspace(len(mats), A, k, int(c), ctypes.byref(n)), "cmrs_spmm_plan_workspace")
+        need = max(need, n.value)
+    ws = workspace(need, Xs[0].device)
+    cand = (ctypes.c_int * len(candidates))(*candidates)
+    best, ms = ctypes.c_int(), ctypes.c_float()
+    _check(lib().cmrs_spmm_autotune(len(mats), A, k, Xp, Yp, cand, len(candidates), int(reps), _ptr(ws), need,
+                                    _stream(stream), ctypes.byref(best), ctypes.byref(ms)), "cmrs_spmm_autotune")
+    return best.value, ms.value
+
+
+# ----------------------------------------------------------------------------- selector
+def cmrs_features(row_ptr, col_ind, stream=None):
+    rows = row_ptr.numel() - 1
+    n = ctypes.c_size_t()
+    _check(lib().cmrs_features_workspace(rows, ctypes.byref(n)), "cmrs_features_workspace")
+    ws = workspace(n.value, row_ptr.device)
+    f = torch.empty(NFEAT, dtype=torch.float64, device=row_ptr.device)
+    _check(lib().cmrs_features(rows, col_ind.numel(), _ptr(row_ptr), _ptr(col_ind), _ptr(f), _ptr(ws), n.value,
+                               _stream(stream)), "cmrs_features")
+    return f
+
+
+def mlp_param_count(nin, nh, nout):
+    return int(lib().cmrs_mlp_param_count(nin, nh, nout))
+
+
+def cmrs_mlp_forward(X, params, nh, nout, acts=None, stream=None):
+    B, nin = X.shape
+    if acts is None:
+        acts = torch.empty(B * (4 * nh + nout), dtype=torch.float32, device=X.device)
+    _check(lib().cmrs_mlp_forward(B, nin, nh, nout, _ptr(X), _ptr(params), _ptr(acts), _stream(stream)),
+           "cmrs_mlp_forward")
+    return acts
+
+
+def mlp_output(acts, B, nh, nout):
+    return acts[4 * B * nh:4 * B * nh + B * nout].view(B, nout)
+
+
+def cmrs_mlp_backward(X, T, params, acts, nh, nout, grads=None, scratch=None, loss=None, stream=None):
+    B, nin = X.shape
+    dev = X.device
+    if grads is None:
+        grads = torch.empty_like(params)
+    if scratch is None:
+        scratch = torch.empty(B * (nout + 2 * nh), dtype=torch.float32, device=dev)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+    _check(lib().cmrs_mlp_backward(B, nin, nh, nout, _ptr(X), _ptr(T), _ptr(params), _ptr(acts), _ptr(grads),
+                                   _ptr(scratch), _ptr(loss), _stream(stream)), "cmrs_mlp_backward")
+    return grads, loss
+
+
+def cmrs_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().cmrs_mlp_adam(params.numel(), _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps), _stream(stream)), "cmrs_mlp_adam")
+
+
+def cmrs_select_strip(row_ptr, col_ind, cols, model=None, stream=None):
+    """(height, variant) for a CRS matrix; model: dict(params, mean, scale, nh)
+    of device tensors, or None for the exhaustive autotune."""
+    rows = row_ptr.numel() - 1
+    nnz = col_ind.numel()
+    n = ctypes.c_size_t()
+    _check(lib().cmrs_select_strip_workspace(rows, cols, nnz, int(model is None), ctypes.byref(n)),
+           "cmrs_select_strip_workspace")
+    ws = workspace(n.value, row_ptr.device)
+    sel = None
+    if model is not None:
+        sel = cmrs_selector(NFEAT, int(model["nh"]), SEL_CHOICES, model["params"].data_ptr(),
+                            model["mean"].data_ptr(), model["scale"].data_ptr())
+    h, v = ctypes.c_int(), ctypes.c_int()
+    _check(lib().cmrs_select_strip(rows, cols, nnz, _ptr(row_ptr), _ptr(col_ind),
+                                   ctypes.byref(sel) if sel is not None else None, ctypes.byref(h), ctypes.byref(v),
+                                   _ptr(ws), n.value, _stream(stream)), "cmrs_select_strip")
+    return h.value, v.value

@@ -1,0 +1,476 @@
+// Strip selector: per-matrix features on the device, a small MLP (forward,
+// backward, Adam) in FP32, and cmrs_select_strip.  Not in the paper: Section
+// 6.2 picks the strip height by brute force over all heights and Section 6.7
+// measures how much per-matrix tuning gains; here a network trained on this
+// library's own timings predicts the choice, with the brute-force sweep as
+// fallback and as the judge of its regret.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cmrs {
+namespace {
+
+constexpr int kNFeat = 24;
+constexpr int kHeights[6] = {1, 2, 4, 8, 16, 32};
+
+struct FeatAcc {
+  unsigned long long sum_l2, max_l, empty, same, near, sum_d, max_d;
+  unsigned long long bins[8];
+  unsigned long long spread[6], nonempty[6];
+};
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One warp per row: row length statistics, |col - row| statistics and the
+// row's min/max column (for the strip spreads).
+__global__ void k_feat_rows(int rows, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            int32_t *__restrict__ rmin, int32_t *__restrict__ rmax, FeatAcc *acc) {
+  __shared__ unsigned long long s[15];
+  if (threadIdx.x < 15) s[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long l2 = 0, mxl = 0, empty = 0, same = 0, near = 0, sd = 0, mxd = 0;
+  unsigned long long bins[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += nw) {
+    const int a = rp[i], b = rp[i + 1];
+    unsigned long long d_sum = 0, d_max = 0, d_near = 0;
+    int lo = INT32_MAX, hi = -1;
+    for (int k = a + lane; k < b; k += 32) {
+      const int c = ci[k];
+      const long long d = (long long)c - i;
+      const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+      d_sum += ad;
+      d_max = max(d_max, ad);
+      d_near += ad <= 64 ? 1ull : 0ull;
+      lo = min(lo, c);
+      hi = max(hi, c);
+    }
+    d_sum = warp_sum(d_sum);
+    d_max = warp_max(d_max);
+    d_near = warp_sum(d_near);
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      const unsigned long long l = (unsigned long long)(b - a);
+      l2 += l * l;
+      mxl = max(mxl, l);
+      empty += l == 0;
+      if (i > 0 && l == (unsigned long long)(a - rp[i - 1])) same++;
+      if (l >= 1) {
+        int bb = 0;
+        while (bb < 7 && l >= (2ull << bb)) ++bb;
+        bins[bb]++;
+      }
+      sd += d_sum;
+      mxd = max(mxd, d_max);
+      near += d_near;
+      rmin[i] = lo;
+      rmax[i] = hi;
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&s[0], l2);
+    atomicMax(&s[1], mxl);
+    atomicAdd(&s[2], empty);
+    atomicAdd(&s[3], same);
+    atomicAdd(&s[4], near);
+    atomicAdd(&s[5], sd);
+    atomicMax(&s[6], mxd);
+    for (int bb = 0; bb < 8; ++bb) atomicAdd(&s[7 + bb], bins[bb]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&acc->sum_l2, s[0]);
+    atomicMax(&acc->max_l, s[1]);
+    atomicAdd(&acc->empty, s[2]);
+    atomicAdd(&acc->same, s[3]);
+    atomicAdd(&acc->near, s[4]);
+    atomicAdd(&acc->sum_d, s[5]);
+    atomicMax(&acc->max_d, s[6]);
+    for (int bb = 0; bb < 8; ++bb) atomicAdd(&acc->bins[bb], s[7 + bb]);
+  }
+}
+
+// blockIdx.y = height index e (h = 2^e): spread of strip s = max - min column
+// over its rows, summed over non-empty strips.
+__global__ void k_feat_strips(int rows, const int32_t *__restrict__ rmin, const int32_t *__restrict__ rmax,
+                              FeatAcc *acc) {
+  __shared__ unsigned long long s_spread, s_nonempty;
+  if (threadIdx.x == 0) {
+    s_spread = 0;
+    s_nonempty = 0;
+  }
+  __syncthreads();
+  const int e = blockIdx.y;
+  const int h = 1 << e;
+  const long long strips = (rows + (long long)h - 1) / h;
+  unsigned long long sp = 0, ne = 0;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < strips;
+       s += (long long)gridDim.x * blockDim.x) {
+    int lo = INT32_MAX, hi = -1;
+    const long long r1 = min((s + 1) * h, (long long)rows);
+    for (long long r = s * h; r < r1; ++r) {
+      lo = min(lo, rmin[r]);
+      hi = max(hi, rmax[r]);
+    }
+    if (hi >= 0) {
+      sp += (unsigned long long)(hi - lo);
+      ne++;
+    }
+  }
+  sp = warp_sum(sp);
+  ne = warp_sum(ne);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_spread, sp);
+    atomicAdd(&s_nonempty, ne);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&acc->spread[e], s_spread);
+    atomicAdd(&acc->nonempty[e], s_nonempty);
+  }
+}
+
+// The 24 features from the integer sums, with the same operations, in the
+// same order, as their definition (no contraction into FMAs).
+__global__ void k_feat_final(int rows, int nnz, const FeatAcc *acc, double *f) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double n = (double)rows, z = (double)nnz;
+  const double mu = __ddiv_rn(z, n);
+  double var = __dsub_rn(__ddiv_rn((double)acc->sum_l2, n), __dmul_rn(mu, mu));
+  if (var < 0.0) var = 0.0;
+  f[0] = log2(n);
+  f[1] = log2(z > 1.0 ? z : 1.0);
+  f[2] = log2(__dadd_rn(1.0, mu));
+  f[3] = __ddiv_rn(sqrt(var), mu > 1.0 ? mu : 1.0);
+  f[4] = log2(__dadd_rn(1.0, (double)acc->max_l));
+  f[5] = __ddiv_rn((double)acc->empty, n);
+  for (int b = 0; b < 8; ++b) f[6 + b] = __ddiv_rn((double)acc->bins[b], n);
+  f[14] = log2(__dadd_rn(1.0, nnz > 0 ? __ddiv_rn((double)acc->sum_d, z) : 0.0));
+  f[15] = log2(__dadd_rn(1.0, (double)acc->max_d));
+  f[16] = nnz > 0 ? __ddiv_rn((double)acc->near, z) : 0.0;
+  f[17] = rows > 1 ? __ddiv_rn((double)acc->same, (double)(rows - 1)) : 0.0;
+  for (int e = 0; e < 6; ++e) {
+    const double ne = (double)acc->nonempty[e];
+    f[18 + e] = log2(__dadd_rn(1.0, ne > 0 ? __ddiv_rn((double)acc->spread[e], ne) : 0.0));
+  }
+}
+
+// ------------------------------------------------------------------ MLP (FP32)
+// Z[n][j] = b[j] + sum_i W[j][i] X[n][i]; H = relu(Z) (or Z for the output).
+__global__ void k_dense_fwd(int B, int nin, int nout, const float *__restrict__ X, const float *__restrict__ W,
+                            const float *__restrict__ bias, float *__restrict__ Z, float *__restrict__ H, int relu) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * nout) return;
+  const int n = t / nout, j = t - n * nout;
+  float s = bias[j];
+  for (int i = 0; i < nin; ++i) s = fmaf(W[j * nin + i], X[n * nin + i], s);
+  if (Z) Z[t] = s;
+  if (H) H[t] = relu ? fmaxf(s, 0.f) : s;
+}
+
+// gO = (O - T) / (B * nout); loss = sum (O - T)^2 / (2 B nout), one block.
+__global__ void k_out_grad(int total, float scale, const float *__restrict__ O, const float *__restrict__ T,
+                           float *__restrict__ G, float *loss) {
+  __shared__ float part[256];
+  float s = 0.f;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const float e = O[i] - T[i];
+    G[i] = e * scale;
+    s = fmaf(e, e, s);
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) *loss = 0.5f * part[0] * scale;
+}
+
+// dW[j][i] = sum_n G[n][j] H[n][i]; db[j] = sum_n G[n][j] (thread per (j, i),
+// i == nin for the bias); sums run over n in order.
+__global__ void k_weight_grad(int B, int nin, int nout, const float *__restrict__ G, const float *__restrict__ H,
+                              float *__restrict__ dW, float *__restrict__ db) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nout * (nin + 1)) return;
+  const int j = t / (nin + 1), i = t - j * (nin + 1);
+  float s = 0.f;
+  if (i < nin) {
+    for (int n = 0; n < B; ++n) s = fmaf(G[n * nout + j], H[n * nin + i], s);
+    dW[j * nin + i] = s;
+  } else {
+    for (int n = 0; n < B; ++n) s += G[n * nout + j];
+    db[j] = s;
+  }
+}
+
+// Gin[n][i] = (Z[n][i] > 0) * sum_j W[j][i] G[n][j]
+__global__ void k_back_hidden(int B, int nin, int nout, const float *__restrict__ G, const float *__restrict__ W,
+                              const float *__restrict__ Z, float *__restrict__ Gin) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * nin) return;
+  const int n = t / nin, i = t - n * nin;
+  float s = 0.f;
+  for (int j = 0; j < nout; ++j) s = fmaf(W[j * nin + i], G[n * nout + j], s);
+  Gin[t] = Z[t] > 0.f ? s : 0.f;
+}
+
+// Adam (Kingma and Ba 2015); c1 = 1 - beta1^t, c2 = 1 - beta2^t.
+__global__ void k_adam(int n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// x = (f - mean) * scale as FP32 network input; then the argmin of the
+// network's predicted cost over the choices.
+__global__ void k_normalize(int nf, const double *__restrict__ f, const float *__restrict__ mean,
+                            const float *__restrict__ scale, float *__restrict__ x) {
+  const int i = threadIdx.x;
+  if (i < nf) x[i] = ((float)f[i] - mean[i]) * scale[i];
+}
+
+__global__ void k_argmin(int n, const float *__restrict__ o, int *__restrict__ out) {
+  if (threadIdx.x != 0) return;
+  int best = 0;
+  for (int i = 1; i < n; ++i)
+    if (o[i] < o[best]) best = i;
+  *out = best;
+}
+
+inline int grid_for(long long n, int t) { return (int)std::max<long long>(1, (n + t - 1) / t); }
+
+size_t param_count(int nin, int nh, int nout) {
+  return (size_t)nh * nin + nh + (size_t)nh * nh + nh + (size_t)nout * nh + nout;
+}
+
+size_t features_ws(int rows) { return align256(sizeof(FeatAcc)) + 2 * align256((size_t)std::max(rows, 1) * 4); }
+
+}  // namespace
+}  // namespace cmrs
+
+using namespace cmrs;
+
+extern "C" int cmrs_features_workspace(int rows, size_t *bytes) {
+  if (rows < 0 || !bytes) return CMRS_ERR_ARG;
+  *bytes = features_ws(rows);
+  return CMRS_OK;
+}
+
+extern "C" int cmrs_features(int rows, int nnz, const int32_t *row_ptr, const int32_t *col_ind, double *feat,
+                             void *workspace, size_t workspace_bytes, void *stream) {
+  if (rows < 1 || nnz < 0 || !row_ptr || !feat || (nnz > 0 && !col_ind)) return CMRS_ERR_ARG;
+  if (!workspace || workspace_bytes < features_ws(rows) || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return CMRS_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  char *ws = reinterpret_cast<char *>(workspace);
+  FeatAcc *acc = reinterpret_cast<FeatAcc *>(ws);
+  int32_t *rmin = reinterpret_cast<int32_t *>(ws + align256(sizeof(FeatAcc)));
+  int32_t *rmax = reinterpret_cast<int32_t *>(ws + align256(sizeof(FeatAcc)) + align256((size_t)rows * 4));
+  CMRS_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(FeatAcc), st));
+  const int sms = sm_count();
+  const int g = (int)std::min<long long>(ceil_div((long long)rows * 32, 256), (long long)sms * 8);
+  k_feat_rows<<<g, 256, 0, st>>>(rows, row_ptr, col_ind, rmin, rmax, acc);
+  CMRS_LAUNCH_CHECK();
+  dim3 g2((unsigned)std::min<long long>(ceil_div(rows, 256), (long long)sms * 4), 6);
+  k_feat_strips<<<g2, 256, 0, st>>>(rows, rmin, rmax, acc);
+  CMRS_LAUNCH_CHECK();
+  k_feat_final<<<1, 32, 0, st>>>(rows, nnz, acc, feat);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
+extern "C" int64_t cmrs_mlp_param_count(int nin, int nh, int nout) {
+  if (nin < 1 || nh < 1 || nout < 1) return -1;
+  return (int64_t)param_count(nin, nh, nout);
+}
+
+// acts layout: Z1[B][nh], H1[B][nh], Z2[B][nh], H2[B][nh], O[B][nout]
+extern "C" int cmrs_mlp_forward(int B, int nin, int nh, int nout, const float *X, const float *params, float *acts,
+                                void *stream) {
+  if (B < 1 || nin < 1 || nh < 1 || nout < 1 || !X || !params || !acts) return CMRS_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  const float *W1 = params, *b1 = W1 + (size_t)nh * nin, *W2 = b1 + nh, *b2 = W2 + (size_t)nh * nh, *W3 = b2 + nh,
+              *b3 = W3 + (size_t)nout * nh;
+  float *Z1 = acts, *H1 = Z1 + (size_t)B * nh, *Z2 = H1 + (size_t)B * nh, *H2 = Z2 + (size_t)B * nh,
+        *O = H2 + (size_t)B * nh;
+  k_dense_fwd<<<grid_for((long long)B * nh, 128), 128, 0, st>>>(B, nin, nh, X, W1, b1, Z1, H1, 1);
+  k_dense_fwd<<<grid_for((long long)B * nh, 128), 128, 0, st>>>(B, nh, nh, H1, W2, b2, Z2, H2, 1);
+  k_dense_fwd<<<grid_for((long long)B * nout, 128), 128, 0, st>>>(B, nh, nout, H2, W3, b3, nullptr, O, 0);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
+// Loss 1/(2 B nout) sum (O - T)^2 and its gradient (same layout as params).
+// scratch: B * (nout + 2 nh) floats.  loss: device float (may be NULL).
+extern "C" int cmrs_mlp_backward(int B, int nin, int nh, int nout, const float *X, const float *T,
+                                 const float *params, const float *acts, float *grads, float *scratch, float *loss,
+                                 void *stream) {
+  if (B < 1 || nin < 1 || nh < 1 || nout < 1 || !X || !T || !params || !acts || !grads || !scratch)
+    return CMRS_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  const float *W2 = params + (size_t)nh * nin + nh, *W3 = W2 + (size_t)nh * nh + nh;
+  const float *Z1 = acts, *H1 = Z1 + (size_t)B * nh, *Z2 = H1 + (size_t)B * nh, *H2 = Z2 + (size_t)B * nh,
+              *O = H2 + (size_t)B * nh;
+  float *dW1 = grads, *db1 = dW1 + (size_t)nh * nin, *dW2 = db1 + nh, *db2 = dW2 + (size_t)nh * nh,
+        *dW3 = db2 + nh, *db3 = dW3 + (size_t)nout * nh;
+  float *gO = scratch, *g2 = gO + (size_t)B * nout, *g1 = g2 + (size_t)B * nh;
+  const float scale = 1.0f / ((float)B * (float)nout);
+  k_out_grad<<<1, 256, 0, st>>>(B * nout, scale, O, T, gO, loss);
+  k_weight_grad<<<grid_for((long long)nout * (nh + 1), 128), 128, 0, st>>>(B, nh, nout, gO, H2, dW3, db3);
+  k_back_hidden<<<grid_for((long long)B * nh, 128), 128, 0, st>>>(B, nh, nout, gO, W3, Z2, g2);
+  k_weight_grad<<<grid_for((long long)nh * (nh + 1), 128), 128, 0, st>>>(B, nh, nh, g2, H1, dW2, db2);
+  k_back_hidden<<<grid_for((long long)B * nh, 128), 128, 0, st>>>(B, nh, nh, g2, W2, Z1, g1);
+  k_weight_grad<<<grid_for((long long)nh * (nin + 1), 128), 128, 0, st>>>(B, nin, nh, g1, X, dW1, db1);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
+extern "C" int cmrs_mlp_adam(int n, float *params, const float *grads, float *m, float *v, int step, float lr,
+                             float beta1, float beta2, float eps, void *stream) {
+  if (n < 1 || !params || !grads || !m || !v || step < 1) return CMRS_ERR_ARG;
+  const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+  k_adam<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(n, params, grads, m, v, lr, beta1, beta2, eps, c1, c2);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
+// ------------------------------------------------------------------ selection
+static size_t select_ws(int rows, int cols, int nnz, int exhaustive) {
+  size_t b = features_ws(rows) + align256(kNFeat * 8) + align256(1024 * 4) + align256(64);
+  if (exhaustive) {
+    const size_t strips = (size_t)rows + 1;
+    b += align256(strips * 4) + align256((size_t)std::max(nnz, 1) * 4) * 3 + align256((size_t)std::max(cols, 1) * 4) +
+         align256((size_t)std::max(rows, 1) * 4);
+    size_t s = 0;
+    cmrs_from_csr_workspace(rows, nnz, 1, 0, CMRS_F32, &s);
+    b += align256(s);
+    b += align256(256 + ((size_t)nnz / 1920 + 2) * 40 + 4096);
+  }
+  return b;
+}
+
+extern "C" int cmrs_select_strip_workspace(int rows, int cols, int nnz, int exhaustive, size_t *bytes) {
+  if (rows < 1 || cols < 1 || nnz < 0 || !bytes) return CMRS_ERR_ARG;
+  *bytes = select_ws(rows, cols, nnz, exhaustive);
+  return CMRS_OK;
+}
+
+__global__ void k_fill(float *p, long long n, float v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row_ptr, const int32_t *col_ind,
+                                 const cmrs_selector *model, int *height_out, int *variant_out, void *workspace,
+                                 size_t workspace_bytes, void *stream) {
+  if (rows < 1 || cols < 1 || nnz < 0 || !row_ptr || !height_out || !variant_out) return CMRS_ERR_ARG;
+  const int exhaustive = model == nullptr;
+  const size_t need = select_ws(rows, cols, nnz, exhaustive);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CMRS_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  char *ws = reinterpret_cast<char *>(workspace);
+  size_t off = features_ws(rows);
+  double *feat = reinterpret_cast<double *>(ws + off);
+  off += align256(kNFeat * 8);
+  float *buf = reinterpret_cast<float *>(ws + off);
+  off += align256(1024 * 4);
+  int *choice = reinterpret_cast<int *>(ws + off);
+  off += align256(64);
+  if (!exhaustive) {
+    if (model->nin != kNFeat || model->nout != 3 * 6 || model->nh < 1 || model->nh > 64 || !model->params ||
+        !model->feat_mean || !model->feat_scale)
+      return CMRS_ERR_ARG;
+    int rc = cmrs_features(rows, nnz, row_ptr, col_ind, feat, workspace, features_ws(rows), stream);
+    if (rc) return rc;
+    const int nh = model->nh, nout = model->nout;
+    float *x = buf, *acts = buf + 32;  // 4*nh + nout <= 4*64 + 18 floats fit in the 992 left
+    k_normalize<<<1, 32, 0, st>>>(kNFeat, feat, model->feat_mean, model->feat_scale, x);
+    rc = cmrs_mlp_forward(1, kNFeat, nh, nout, x, model->params, acts, stream);
+    if (rc) return rc;
+    k_argmin<<<1, 32, 0, st>>>(nout, acts + 4 * nh, choice);
+    CMRS_LAUNCH_CHECK();
+    int c = 0;
+    CMRS_CUDA_TRY(cudaMemcpyAsync(&c, choice, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CMRS_CUDA_TRY(cudaStreamSynchronize(st));
+    *height_out = kHeights[c / 3];
+    *variant_out = c % 3;
+    return CMRS_OK;
+  }
+  // Exhaustive autotune (Section 6.2's brute force): convert with every
+  // height and time every variant; the values are ones (timing does not
+  // depend on them).
+  int32_t *sp = reinterpret_cast<int32_t *>(ws + off);
+  off += align256(((size_t)rows + 1) * 4);
+  uint32_t *pk = reinterpret_cast<uint32_t *>(ws + off);
+  off += align256((size_t)std::max(nnz, 1) * 4);
+  float *val = reinterpret_cast<float *>(ws + off);
+  off += align256((size_t)std::max(nnz, 1) * 4);
+  float *ones = reinterpret_cast<float *>(ws + off);
+  off += align256((size_t)std::max(nnz, 1) * 4);
+  float *x = reinterpret_cast<float *>(ws + off);
+  off += align256((size_t)cols * 4);
+  float *y = reinterpret_cast<float *>(ws + off);
+  off += align256((size_t)rows * 4);
+  size_t cws = 0;
+  cmrs_from_csr_workspace(rows, nnz, 1, 0, CMRS_F32, &cws);
+  char *conv_ws = ws + off;
+  off += align256(cws);
+  char *spmv_ws = ws + off;
+  const size_t spmv_bytes = workspace_bytes - off;
+  k_fill<<<grid_for(std::max(nnz, 1), 256), 256, 0, st>>>(ones, std::max(nnz, 1), 1.f);
+  k_fill<<<grid_for(cols, 256), 256, 0, st>>>(x, cols, 1.f);
+  CMRS_LAUNCH_CHECK();
+  CMRS_CUDA_TRY(cudaMemsetAsync(spmv_ws, 0, 256, st));
+  cudaEvent_t e0, e1;
+  CMRS_CUDA_TRY(cudaEventCreate(&e0));
+  CMRS_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bh = 4, bv = 0, rc = CMRS_OK;
+  for (int hi = 0; hi < 6 && rc == CMRS_OK; ++hi) {
+    cmrs_matrix A;
+    rc = cmrs_from_csr(rows, cols, nnz, row_ptr, col_ind, ones, CMRS_F32, kHeights[hi], 0, CMRS_F32, sp, pk, val,
+                       conv_ws, cws, stream, &A);
+    for (int v = 0; v < 3 && rc == CMRS_OK; ++v) {
+      for (int w = 0; w < 2 && rc == CMRS_OK; ++w) rc = cmrs_spmv(&A, x, y, v, spmv_ws, spmv_bytes, stream);
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 5 && rc == CMRS_OK; ++r) rc = cmrs_spmv(&A, x, y, v, spmv_ws, spmv_bytes, stream);
+      cudaEventRecord(e1, st);
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess && rc == CMRS_OK) rc = set_cuda_error(e);
+      if (rc == CMRS_OK && ms < best) {
+        best = ms;
+        bh = kHeights[hi];
+        bv = v;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  *height_out = bh;
+  *variant_out = bv;
+  return CMRS_OK;
+}

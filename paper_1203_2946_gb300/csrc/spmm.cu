@@ -297,7 +297,7 @@ extern "C" int cmrs_spmm_plan_create(int batch, const cmrs_matrix *const *A, con
   return CMRS_OK;
 }
 
-extern "C" int cmrs_spmm_plan_execute(cmrs_spmm_plan *p, void *stream) {
+extern "C" int cmrs_spmm_batched(cmrs_spmm_plan *p, void *stream) {
   if (!p) return CMRS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   if (p->exec) {
@@ -343,9 +343,9 @@ extern "C" int cmrs_spmm_autotune(int batch, const cmrs_matrix *const *A, const 
     cmrs_spmm_plan *p = nullptr;
     rc = cmrs_spmm_plan_create(batch, A, k, X, Y, candidates[c], 1, workspace, workspace_bytes, stream, &p);
     if (rc) break;
-    for (int w = 0; w < 2 && rc == CMRS_OK; ++w) rc = cmrs_spmm_plan_execute(p, stream);
+    for (int w = 0; w < 2 && rc == CMRS_OK; ++w) rc = cmrs_spmm_batched(p, stream);
     cudaEventRecord(e0, st);
-    for (int r = 0; r < reps && rc == CMRS_OK; ++r) rc = cmrs_spmm_plan_execute(p, stream);
+    for (int r = 0; r < reps && rc == CMRS_OK; ++r) rc = cmrs_spmm_batched(p, stream);
     cudaEventRecord(e1, st);
     cudaError_t e = cudaEventSynchronize(e1);
     float ms = 0.f;

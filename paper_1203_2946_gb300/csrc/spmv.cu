@@ -97,29 +97,28 @@ __device__ __forceinline__ int lb_ris(const uint32_t *cp, long long base, int lo
 }
 
 // Dot product of entries [lo, hi) with x, in storage order, one FMA each.
+// The column words and x gathers of CH consecutive entries are issued before
+// their FMAs, so a row costs ceil(len / CH) round trips to L2, not len.
+template <int DT>
+struct DotChunk {
+  static constexpr int kCH = DT == CMRS_F64 ? 16 : 32;
+};
+
 template <int DT>
 __device__ __forceinline__ typename Form<DT>::Acc row_dot(const uint32_t *cp, const typename Form<DT>::Stored *vh,
                                                           const typename Form<DT>::Stored *vl, long long base, int lo,
                                                           int hi, int bits, const typename Form<DT>::Acc *x) {
   typedef typename Form<DT>::Acc A;
+  constexpr int CH = DotChunk<DT>::kCH;
   A acc = A(0);
-  int k = lo;
-  for (; k + 4 <= hi; k += 4) {
-    const long long i = k - base;
-    const uint32_t c0 = cp[i], c1 = cp[i + 1], c2 = cp[i + 2], c3 = cp[i + 3];
-    const A x0 = ld_x(x + (c0 >> bits)), x1 = ld_x(x + (c1 >> bits)), x2 = ld_x(x + (c2 >> bits)),
-            x3 = ld_x(x + (c3 >> bits));
-    const A v0 = Form<DT>::value(vh, vl, i), v1 = Form<DT>::value(vh, vl, i + 1), v2 = Form<DT>::value(vh, vl, i + 2),
-            v3 = Form<DT>::value(vh, vl, i + 3);
-    acc = fma_acc(v0, x0, acc);
-    acc = fma_acc(v1, x1, acc);
-    acc = fma_acc(v2, x2, acc);
-    acc = fma_acc(v3, x3, acc);
-  }
-  for (; k < hi; ++k) {
-    const long long i = k - base;
-    const uint32_t c = cp[i];
-    acc = fma_acc(Form<DT>::value(vh, vl, i), ld_x(x + (c >> bits)), acc);
+  for (int k = lo; k < hi; k += CH) {
+    A xv[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j)
+      if (k + j < hi) xv[j] = ld_x(x + (cp[k + j - base] >> bits));
+#pragma unroll
+    for (int j = 0; j < CH; ++j)
+      if (k + j < hi) acc = fma_acc(Form<DT>::value(vh, vl, k + j - base), xv[j], acc);
   }
   return acc;
 }
@@ -175,40 +174,39 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_row(int rows, int height, 
   for (int it = 0; b < nblk; ++it, b += gridDim.x) {
     const int st = it & 1;
     if (tid == 0 && b + (int)gridDim.x < nblk) issue(b + gridDim.x, st ^ 1);
-    if (!mbar_wait_bounded(&bars[st], (it >> 1) & 1)) {
+    // this thread's row and its strip bounds: loaded before the wait so the
+    // latency overlaps the bulk copy
+    const long long row = (long long)b * kRowThreads + tid;
+    const bool active = row < rows;
+    const int s = active ? (int)(row / height) : 0;
+    const uint32_t r = (uint32_t)(row - (long long)s * height);
+    const int sa = active ? sp[s] : 0, sb = active ? sp[s + 1] : 0;
+    const bool ok = mbar_wait_bounded(&bars[st], (it >> 1) & 1);
+    if (!ok) {
       s_abort = 1;
       atomicOr(status, ST_TIMEOUT);
-    } else {
-      const long long row = (long long)b * kRowThreads + tid;
-      if (row < rows) {
-        const int s = (int)(row / height);
-        const uint32_t r = (uint32_t)(row - (long long)s * height);
-        const int sa = sp[s], sb = sp[s + 1];
-        typename Form<DT>::Acc acc;
-        if (info[st].staged) {
-          const char *stg = smem + st * stage_bytes;
-          const uint32_t *cp = reinterpret_cast<const uint32_t *>(stg);
-          const S *vh = reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kRowCap));
-          const S *vl = reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kRowCap) + Stage<DT>::val_bytes(kRowCap));
-          const long long base = info[st].a8;
-          int k0 = sa, k1 = sb;
-          if (height > 1) {
-            k0 = lb_ris(cp, base, sa, sb, r, mask);
-            k1 = lb_ris(cp, base, k0, sb, r + 1, mask);
-          }
-          acc = row_dot<DT>(cp, vh, vl, base, k0, k1, bits, x);
-        } else {
-          const S *vl = Stage<DT>::kSplit ? lo : hi;
-          int k0 = sa, k1 = sb;
-          if (height > 1) {
-            k0 = lb_ris(packed, 0, sa, sb, r, mask);
-            k1 = lb_ris(packed, 0, k0, sb, r + 1, mask);
-          }
-          acc = row_dot<DT>(packed, hi, vl, 0, k0, k1, bits, x);
-        }
-        y[row] = acc;
-      }
     }
+    const bool staged = info[st].staged;
+    const char *stg = smem + st * stage_bytes;
+    const uint32_t *cp = staged ? reinterpret_cast<const uint32_t *>(stg) : packed;
+    const S *vh = staged ? reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kRowCap)) : hi;
+    const S *vl = staged ? reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(kRowCap) +
+                                                       Stage<DT>::val_bytes(kRowCap))
+                         : (Stage<DT>::kSplit ? lo : hi);
+    const long long base = staged ? info[st].a8 : 0;
+    // row bounds: the first entry with RowInStrip >= r starts the row; the
+    // next row's start (held by the next lane when it is in the same strip)
+    // ends it
+    const bool run = ok && active;
+    int k0 = sa;
+    if (run && r > 0) k0 = lb_ris(cp, base, sa, sb, r, mask);
+    const int nxt = __shfl_down_sync(0xffffffffu, k0, 1);
+    int k1 = sb;
+    if (run && r + 1 < (uint32_t)height && row + 1 < rows) {
+      if ((tid & 31) < 31) k1 = nxt;
+      else k1 = lb_ris(cp, base, k0, sb, r + 1, mask);
+    }
+    if (run) y[row] = row_dot<DT>(cp, vh, vl, base, k0, k1, bits, x);
     __syncthreads();
     if (s_abort) break;
   }

@@ -1,0 +1,185 @@
+"""The learned strip selector: timing corpus, training, regret.
+
+Section 6.2 of the paper picks the strip height by brute force and Section
+6.7 reports what per-matrix tuning gains.  Here the brute force is this
+library's exhaustive sweep (6 heights x 3 kernel variants, timed with CUDA
+events on the device), and a small network trained on those timings predicts
+the choice from 24 structural features.  Every numeric step -- features,
+conversion, SpMV timing, the network's forward and backward passes and the
+Adam updates -- runs in libcmrs kernels; this module only orchestrates.
+
+Choice c = 3 * height_index + variant, height_index over (1, 2, 4, 8, 16, 32),
+variant 0 ROW, 1 STRIP, 2 MERGE.  The network regresses the cost of every
+choice relative to the best one, log2(t_c / t_best), and the smallest
+predicted cost wins.
+"""
+from __future__ import annotations
+
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+
+import numpy as np
+import torch
+
+from . import binding as b
+from . import inputs
+
+HEIGHTS = b.SEL_HEIGHTS
+NCHOICE = b.SEL_CHOICES
+NH = 64
+FORMAT_VERSION = 1
+
+
+def choice_name(c):
+    return "h=%d/%s" % (HEIGHTS[c // 3], ("row", "strip", "merge")[c % 3])
+
+
+# ----------------------------------------------------------------------------- timing
+class Timer:
+    """Times cmrs_spmv calls with CUDA events, L2 flushed before each call."""
+
+    def __init__(self, device, flush_bytes=256 << 20):
+        self.flush = torch.empty(flush_bytes, dtype=torch.uint8, device=device)
+        self.n = 0
+
+    def time(self, fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        for i in range(reps):
+            self.n += 1
+            self.flush.fill_(self.n & 0xFF)
+            st[i].record()
+            fn()
+            en[i].record()
+        torch.cuda.synchronize()
+        return statistics.median(s.elapsed_time(e) for s, e in zip(st, en))
+
+
+def time_all_choices(a: inputs.CSR, timer: Timer, device, reps=5):
+    """Exhaustive sweep: ms per SpMV for each of the 18 choices (FP32 values)."""
+    rp = torch.from_numpy(a.row_ptr).to(device)
+    ci = torch.from_numpy(a.col_ind).to(device)
+    va = torch.from_numpy(np.ascontiguousarray(a.val, dtype=np.float32)).to(device)
+    x = torch.ones(a.cols, dtype=torch.float32, device=device)
+    y = torch.empty(a.rows, dtype=torch.float32, device=device)
+    out = np.zeros(NCHOICE)
+    for hi, h in enumerate(HEIGHTS):
+        M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F32)
+        for v in range(3):
+            ws = M.spmv_workspace(v)
+            out[3 * hi + v] = timer.time(lambda: b.cmrs_spmv(M, x, y, v, ws), reps=reps)
+        del M
+    feat = b.cmrs_features(rp, ci).cpu().numpy()
+    return feat, out
+
+
+def _gen(spec):
+    a = inputs.selector_matrix(spec)
+    return a.rows, a.cols, a.row_ptr, a.col_ind, np.ascontiguousarray(a.val, dtype=np.float32)
+
+
+def build_corpus(specs, device="cuda", reps=5, workers=None, log=None):
+    """Features and exhaustive timings for every spec.  Matrices are generated
+    on host processes started with `spawn` (safe next to a CUDA context)."""
+    timer = Timer(device)
+    feats, times = [], []
+    workers = workers or max(1, min(12, (os.cpu_count() or 2) - 2))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        for i, (rows, cols, rp, ci, val) in enumerate(pool.imap(_gen, specs, chunksize=2)):
+            a = inputs.CSR(rows, cols, rp, ci, val)
+            f, t = time_all_choices(a, timer, device, reps)
+            feats.append(f)
+            times.append(t)
+            if log and (i % 100 == 0 or i == len(specs) - 1):
+                log("corpus %d/%d  n=%d nnz=%d best=%s" % (i + 1, len(specs), rows, a.nnz, choice_name(int(t.argmin()))))
+    return np.array(feats), np.array(times)
+
+
+# ----------------------------------------------------------------------------- network
+def targets_from_times(times):
+    return np.log2(times / times.min(axis=1, keepdims=True)).astype(np.float32)
+
+
+def init_params(seed=0, nin=b.NFEAT, nh=NH, nout=NCHOICE):
+    """He-normal weights, zero biases (layout of cmrs_mlp_*)."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, math.sqrt(2.0 / nin), (nh, nin)), np.zeros(nh),
+             rng.normal(0, math.sqrt(2.0 / nh), (nh, nh)), np.zeros(nh),
+             rng.normal(0, math.sqrt(1.0 / nh), (nout, nh)), np.zeros(nout)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def normalization(features):
+    mean = features.mean(axis=0)
+    std = features.std(axis=0)
+    scale = np.where(std > 1e-12, 1.0 / np.maximum(std, 1e-12), 0.0)
+    return mean.astype(np.float32), scale.astype(np.float32)
+
+
+def train(features, times, idx, steps=3000, batch=256, lr=2e-3, seed=0, device="cuda", log=None):
+    """Trains on rows `idx` with the library's forward/backward/Adam kernels."""
+    mean, scale = normalization(features[idx])
+    X = torch.from_numpy(((features[idx] - mean) * scale).astype(np.float32)).to(device)
+    T = torch.from_numpy(targets_from_times(times[idx])).to(device)
+    P = torch.from_numpy(init_params(seed)).to(device)
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    n = X.shape[0]
+    rng = np.random.default_rng(seed + 1)
+    B = min(batch, n)
+    acts = torch.empty(B * (4 * NH + NCHOICE), dtype=torch.float32, device=device)
+    grads = torch.empty_like(P)
+    scratch = torch.empty(B * (NCHOICE + 2 * NH), dtype=torch.float32, device=device)
+    loss = torch.empty(1, dtype=torch.float32, device=device)
+    history = []
+    for step in range(1, steps + 1):
+        sel = torch.from_numpy(rng.choice(n, B, replace=False)).to(device)
+        xb, tb = X.index_select(0, sel).contiguous(), T.index_select(0, sel).contiguous()
+        b.cmrs_mlp_forward(xb, P, NH, NCHOICE, acts)
+        b.cmrs_mlp_backward(xb, tb, P, acts, NH, NCHOICE, grads, scratch, loss)
+        b.cmrs_mlp_adam(P, grads, m, v, step, lr)
+        if step % 250 == 0 or step == 1:
+            history.append((step, float(loss.item())))
+            if log:
+                log("train step %d loss %.5f" % history[-1])
+    return {"params": P, "mean": torch.from_numpy(mean).to(device), "scale": torch.from_numpy(scale).to(device),
+            "nh": NH, "history": history}
+
+
+def predict(model, features, device="cuda"):
+    X = torch.from_numpy(((features - model["mean"].cpu().numpy()) * model["scale"].cpu().numpy())
+                         .astype(np.float32)).to(device)
+    acts = b.cmrs_mlp_forward(X, model["params"], model["nh"], NCHOICE)
+    return b.mlp_output(acts, X.shape[0], model["nh"], NCHOICE).argmin(dim=1).cpu().numpy()
+
+
+def regret(times, choice):
+    r = times[np.arange(times.shape[0]), choice] / times.min(axis=1)
+    return {"geomean": float(np.exp(np.mean(np.log(r)))), "median": float(np.median(r)),
+            "p90": float(np.percentile(r, 90)), "max": float(r.max()),
+            "within_10pct": float(np.mean(r <= 1.10))}
+
+
+def split(n, held_out=500, seed=0):
+    perm = np.random.default_rng(seed).permutation(n)
+    return np.sort(perm[held_out:]), np.sort(perm[:held_out])
+
+
+def save_model(model, path, extra=None):
+    np.savez(path, params=model["params"].cpu().numpy(), mean=model["mean"].cpu().numpy(),
+             scale=model["scale"].cpu().numpy(), nh=model["nh"], version=FORMAT_VERSION,
+             extra=json.dumps(extra or {}))
+
+
+def load_model(path, device="cuda"):
+    d = np.load(path)
+    if int(d["version"]) != FORMAT_VERSION:
+        raise ValueError("selector model format %d, expected %d" % (int(d["version"]), FORMAT_VERSION))
+    return {"params": torch.from_numpy(d["params"]).to(device), "mean": torch.from_numpy(d["mean"]).to(device),
+            "scale": torch.from_numpy(d["scale"]).to(device), "nh": int(d["nh"])}
