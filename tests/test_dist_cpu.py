@@ -1,0 +1,54 @@
+"""The N > 1 host logic of bench.py on CPU: two gloo ranks, rendezvous on
+127.0.0.1, barrier, max-over-ranks of the timing value, and the reference arm
+doing no work on ranks other than 0."""
+import multiprocessing as mp
+import os
+import socket
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
+    sys.path.insert(0, ROOT)
+    import bench
+    r, w, dist = bench.dist_setup(world)
+    bench.barrier(dist)
+    m = bench.max_over_ranks(dist, 1.5 * (rank + 1))
+    bench.barrier(dist)
+    if rank == 1:
+        class A:
+            steps, warmup, height, gpus = 3, 1, 4, 2
+        bench.run_reference(A())  # returns at once: only rank 0 runs the reference arm
+    q.put((r, w, m))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_barrier_and_max():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out == [(0, 2, 3.0), (1, 2, 3.0)]
+
+
+def test_beta_plus_matches_eq_6_1():
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    for nnz, rows, strips, sv in [(55_742_968, 2_097_152, 524_288, 8), (20_224, 4_096, 1_024, 8)]:
+        assert bench.beta_plus(nnz, rows, strips, sv) == oracle.beta(nnz, rows, strips, sv)[1]
