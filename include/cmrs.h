@@ -167,6 +167,25 @@ int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes);
 int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant,
               void *workspace, size_t workspace_bytes, void *stream);
 
+/* SpMV that allocates nothing, for callers that cannot allocate device
+ * memory at all: code that runs inside an allocator or memory-pool callback,
+ * under a pool that forbids growth, or in a runtime that owns every device
+ * buffer and hands out no scratch.  (The paper has no counterpart; this entry
+ * point belongs to the library.)  It computes y = A x exactly as cmrs_spmv
+ * with CMRS_VARIANT_MERGE, same arguments without the workspace, but takes
+ * its scratch from one fixed 2 MiB array compiled into the library (a
+ * file-scope __device__ array, resident on every GPU that loads the library
+ * until the process exits).  Limit: A->nnz <= 111,820,800 (58,240 tiles of
+ * 1,920 entries); larger matrices return CMRS_ERR_WORKSPACE before any device
+ * work.  Unsorted strips only (CMRS_ERR_UNSUPPORTED otherwise).  No
+ * cudaMalloc, cudaFree or other allocating call is made.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current), so make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents:
+ * calls that may overlap on the GPU (two streams, two host threads) race and
+ * their results are undefined.  Asynchronous on `stream`. */
+int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, void *stream);
+
 /* Error status left by the last bounded in-kernel wait on this device's
  * status word inside `workspace` (CMRS_OK or CMRS_ERR_TIMEOUT).  Reads device
  * memory synchronously on `stream`. */

@@ -75,6 +75,7 @@ def lib():
             "cmrs_spmv_workspace": ([M, i, ctypes.POINTER(sz)], i),
             "cmrs_spmv": ([M, vp, vp, i, vp, sz, vp], i),
             "cmrs_spmv_check": ([M, i, vp, vp], i),
+            "cmrs_spmv_noalloc": ([M, vp, vp, vp], i),
             "cmrs_spmm": ([M, i, vp, vp, vp], i),
             "cmrs_spmm_plan_workspace": ([i, vp, vp, i, ctypes.POINTER(sz)], i),
             "cmrs_spmm_plan_create": ([i, vp, vp, vp, vp, i, i, vp, sz, vp, ctypes.POINTER(vp)], i),
@@ -206,6 +207,15 @@ def cmrs_spmv(A: Matrix, x, y=None, variant=CMRS_VARIANT_AUTO, workspace_tensor=
     ws = workspace_tensor if workspace_tensor is not None else A.spmv_workspace(variant)
     rc = lib().cmrs_spmv(A.ref(), _ptr(x), _ptr(y), variant, _ptr(ws), ws.numel(), _stream(stream))
     _check(rc, "cmrs_spmv")
+    return y
+
+
+def cmrs_spmv_noalloc(A: Matrix, x, y=None, stream=None):
+    """y = A x with no workspace and no device allocation by the library (the
+    library's fixed scratch array; see cmrs.h for its limit and sharing)."""
+    if y is None:
+        y = torch.empty(A.rows, dtype=A.x_dtype, device=x.device)
+    _check(lib().cmrs_spmv_noalloc(A.ref(), _ptr(x), _ptr(y), _stream(stream)), "cmrs_spmv_noalloc")
     return y
 
 

@@ -642,3 +642,62 @@ extern "C" int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *wo
   }
   return CMRS_OK;
 }
+
+// ============================================================== fixed-scratch entry point
+// For callers that cannot allocate device memory, cmrs_spmv_noalloc runs the
+// MERGE mapping with its scratch (status word, tile map, tile records) in
+// this fixed array instead of a caller workspace.  It stays resident on every
+// GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char cmrs_noalloc_scratch[size_t(2) << 20];
+
+namespace {
+constexpr size_t kNoAllocBytes = size_t(2) << 20;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};
+
+// Device address of the fixed array on the current device.  Looked up once
+// per device (with that device current); host code must not use the symbol
+// itself, which is only a host-side stand-in.
+int noalloc_scratch(void **out) {
+  int dev = 0;
+  CMRS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return CMRS_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    CMRS_CUDA_TRY(cudaGetSymbolAddress(&p, cmrs_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return CMRS_OK;
+}
+}  // namespace
+
+extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, void *stream) {
+  int rc = check_matrix(A);
+  if (rc) return rc;
+  if (A->flags & CMRS_SORTED) return CMRS_ERR_UNSUPPORTED;
+  if (A->rows == 0) return CMRS_OK;
+  if (!y || (A->nnz > 0 && !x)) return CMRS_ERR_ARG;
+  if (merge_ws_bytes(A->nnz) > kNoAllocBytes) return CMRS_ERR_WORKSPACE;
+  if (A->nnz > 0 && ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(A->val)) & 15))
+    return CMRS_ERR_ARG;
+  void *scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (A->nnz == 0) {
+    CMRS_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)A->rows * (A->dtype == CMRS_F64 ? 8 : 4), st));
+    return CMRS_OK;
+  }
+  // the status word must start at zero; everything else is rewritten per call
+  CMRS_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, st));
+  char *ws = reinterpret_cast<char *>(scratch);
+  switch (A->dtype) {
+    case CMRS_F64: return launch<CMRS_F64>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_F32: return launch<CMRS_F32>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
+  }
+  return CMRS_ERR_ARG;
+}
