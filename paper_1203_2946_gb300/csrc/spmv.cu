@@ -17,8 +17,11 @@
 namespace cmrs {
 namespace {
 
-constexpr int kRowThreads = 128;  // ROW: one CTA = 128 consecutive rows
-constexpr int kRowCap = 4096;     // ROW: entries per shared-memory stage
+#ifndef CMRS_ROW_ROWS
+#define CMRS_ROW_ROWS 128
+#endif
+constexpr int kRowThreads = CMRS_ROW_ROWS;    // ROW: rows per block
+constexpr int kRowCap = 32 * CMRS_ROW_ROWS;   // ROW: entries per shared-memory stage
 constexpr int kMergeThreads = 128;
 constexpr int kMergeE = 15;  // MERGE: entries per thread; odd, so that a warp's shared loads hit 32 banks
 constexpr int kMergeTile = kMergeThreads * kMergeE;
@@ -96,21 +99,68 @@ __device__ __forceinline__ int lb_ris(const uint32_t *cp, long long base, int lo
   return lo;
 }
 
-// Dot product of entries [lo, hi) with x, in storage order, one FMA each.
-// The column words and x gathers of CH consecutive entries are issued before
-// their FMAs, so a row costs ceil(len / CH) round trips to L2, not len.
-template <int DT>
-struct DotChunk {
-  static constexpr int kCH = DT == CMRS_F64 ? 16 : 32;
-};
+// ============================================================== ROW mapping
+// A block is CMRS_ROW_ROWS (default 128) consecutive rows: one contiguous range of
+// the nonzero streams.  A producer warp bulk-copies each block's range into a
+// ring of kRowStages shared-memory stages (full/empty mbarrier pairs, no CTA
+// barrier in the loop) and prefetches the next block's bounds while it
+// waits.  T consumer threads share a row: each walks a contiguous segment of
+// it (its start from a binary search on RowInStrip, which is non-decreasing in
+// an unsorted strip; its end from the next row's start), one FMA per entry,
+// and the T partial sums are joined down a shuffle tree with T - 1 adds.  A block larger than
+// the stage capacity is read from global memory instead.
+#ifndef CMRS_ROW_T_F64
+#define CMRS_ROW_T_F64 4
+#endif
+#ifndef CMRS_ROW_T_F32
+#define CMRS_ROW_T_F32 2
+#endif
+#ifndef CMRS_ROW_STAGES
+#define CMRS_ROW_STAGES 2
+#endif
+constexpr int kRowStages = CMRS_ROW_STAGES;
+
+#ifndef CMRS_ROW_CH
+#define CMRS_ROW_CH 0
+#endif
+#ifndef CMRS_ROW_ILP
+#define CMRS_ROW_ILP 1
+#endif
+// Loading the next block's strip bounds one block ahead pays for FP64 (measured
+// 184 -> 172 us on the 27-point 128^3 matrix) and costs the FP32-accumulated
+// forms (100 -> 131 us), so it is chosen per form.
+#ifndef CMRS_ROW_PREFETCH_F64
+#define CMRS_ROW_PREFETCH_F64 1
+#endif
+#ifndef CMRS_ROW_PREFETCH_F32
+#define CMRS_ROW_PREFETCH_F32 0
+#endif
 
 template <int DT>
-__device__ __forceinline__ typename Form<DT>::Acc row_dot(const uint32_t *cp, const typename Form<DT>::Stored *vh,
+struct RowCfg {
+  static constexpr int T = DT == CMRS_F64 ? CMRS_ROW_T_F64 : CMRS_ROW_T_F32;
+  static constexpr int kConsumers = kRowThreads * T;   // threads
+  static constexpr int kThreads = kConsumers + 32;     // + producer warp
+  // x gathers a thread issues per batch (default: a whole 32-entry row share)
+  static constexpr int kCH = CMRS_ROW_CH > 0 ? CMRS_ROW_CH : ((32 / T) < 8 ? 8 : (32 / T));
+  static constexpr int kILP = CMRS_ROW_ILP;            // independent FMA chains per segment
+  static constexpr bool kPrefetch = DT == CMRS_F64 ? CMRS_ROW_PREFETCH_F64 : CMRS_ROW_PREFETCH_F32;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Partial dot product of entries [lo, hi) with x, one FMA each; CH gathers
+// are issued before their FMAs.
+template <int DT, int CH, int ILP>
+__device__ __forceinline__ typename Form<DT>::Acc seg_dot(const uint32_t *cp, const typename Form<DT>::Stored *vh,
                                                           const typename Form<DT>::Stored *vl, long long base, int lo,
                                                           int hi, int bits, const typename Form<DT>::Acc *x) {
   typedef typename Form<DT>::Acc A;
-  constexpr int CH = DotChunk<DT>::kCH;
-  A acc = A(0);
+  A acc[ILP];
+#pragma unroll
+  for (int i = 0; i < ILP; ++i) acc[i] = A(0);
   for (int k = lo; k < hi; k += CH) {
     A xv[CH];
 #pragma unroll
@@ -118,74 +168,111 @@ __device__ __forceinline__ typename Form<DT>::Acc row_dot(const uint32_t *cp, co
       if (k + j < hi) xv[j] = ld_x(x + (cp[k + j - base] >> bits));
 #pragma unroll
     for (int j = 0; j < CH; ++j)
-      if (k + j < hi) acc = fma_acc(Form<DT>::value(vh, vl, k + j - base), xv[j], acc);
+      if (k + j < hi) acc[j % ILP] = fma_acc(Form<DT>::value(vh, vl, k + j - base), xv[j], acc[j % ILP]);
   }
-  return acc;
+#pragma unroll
+  for (int i = 1; i < ILP; ++i) acc[0] += acc[i];
+  return acc[0];
 }
 
-// ============================================================== ROW mapping
-// CTA b owns rows [128 b, 128 b + 128): the strips holding them are one
-// contiguous range of the nonzero streams, staged by bulk copies two blocks
-// ahead.  Thread t walks row 128 b + t: its bounds inside the strip come from
-// two binary searches on RowInStrip, then one FMA per entry.  A block whose
-// strips exceed the stage capacity is read from global memory instead.
 template <int DT>
-__global__ void __launch_bounds__(kRowThreads) k_spmv_row(int rows, int height, int bits, int nnz,
-                                                          const int32_t *__restrict__ sp,
-                                                          const uint32_t *__restrict__ packed,
-                                                          const typename Form<DT>::Stored *__restrict__ hi,
-                                                          const typename Form<DT>::Stored *__restrict__ lo,
-                                                          const typename Form<DT>::Acc *__restrict__ x,
-                                                          typename Form<DT>::Acc *__restrict__ y, uint32_t *status) {
+__global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int height, int bits, int nnz,
+                                                                   const int32_t *__restrict__ sp,
+                                                                   const uint32_t *__restrict__ packed,
+                                                                   const typename Form<DT>::Stored *__restrict__ hi,
+                                                                   const typename Form<DT>::Stored *__restrict__ lo,
+                                                                   const typename Form<DT>::Acc *__restrict__ x,
+                                                                   typename Form<DT>::Acc *__restrict__ y,
+                                                                   uint32_t *status) {
   typedef typename Form<DT>::Stored S;
+  typedef typename Form<DT>::Acc A;
+  constexpr int T = RowCfg<DT>::T;
+  constexpr int kConsumerWarps = RowCfg<DT>::kConsumers / 32;
   extern __shared__ __align__(128) char smem[];
-  __shared__ uint64_t bars[kStages];
-  __shared__ StageInfo info[kStages];
-  __shared__ int s_abort;
+  __shared__ uint64_t full[kRowStages], empty[kRowStages];
+  __shared__ StageInfo info[kRowStages];
   const int tid = threadIdx.x;
   const int nblk = (rows + kRowThreads - 1) / kRowThreads;
   const uint32_t mask = (1u << bits) - 1;
   const size_t stage_bytes = Stage<DT>::bytes(kRowCap);
   if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < kRowStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumerWarps);
+    }
     fence_barrier_init();
-    s_abort = 0;
   }
   __syncthreads();
-  uint64_t pol = 0;
-  if (tid == 0) pol = policy_evict_first();
 
-  auto issue = [&](int b, int st) {
-    const long long r0 = (long long)b * kRowThreads;
-    const long long r1 = min(r0 + kRowThreads, (long long)rows);
-    const int s0 = (int)(r0 / height), s1 = (int)((r1 - 1) / height);
-    const long long ea = sp[s0], eb = sp[s1 + 1];
-    if (eb - ea <= kRowCap) {
-      issue_stage<DT>(ea, eb, nnz, packed, hi, lo, smem + st * stage_bytes, kRowCap, &bars[st], pol, &info[st]);
-    } else {
-      info[st].staged = 0;
-      info[st].a8 = 0;
-      mbar_arrive_expect_tx(&bars[st], 0);
+  if (tid < 32) {
+    // ---------------- producer warp (one lane)
+    if (tid != 0) return;
+    const uint64_t pol = policy_evict_first();
+    auto bounds = [&](int b, long long &ea, long long &eb) {
+      const long long r0 = (long long)b * kRowThreads;
+      const long long r1 = min(r0 + kRowThreads, (long long)rows);
+      ea = sp[(int)(r0 / height)];
+      eb = sp[(int)((r1 - 1) / height) + 1];
+    };
+    long long ea = 0, eb = 0, nea = 0, neb = 0;
+    int b = blockIdx.x;
+    if (b < nblk) bounds(b, ea, eb);
+    for (int it = 0; b < nblk; ++it, b += gridDim.x) {
+      const int st = it % kRowStages, use = it / kRowStages;
+      const int bn = b + gridDim.x;
+      if (bn < nblk) bounds(bn, nea, neb);  // consumed next iteration
+      if (use > 0 && !mbar_wait_bounded(&empty[st], (use - 1) & 1)) {
+        atomicOr(status, ST_TIMEOUT);
+        return;
+      }
+      if (eb - ea <= kRowCap) {
+        issue_stage<DT>(ea, eb, nnz, packed, hi, lo, smem + st * stage_bytes, kRowCap, &full[st], pol, &info[st]);
+      } else {
+        info[st].staged = 0;
+        info[st].a8 = 0;
+        mbar_arrive_expect_tx(&full[st], 0);
+      }
+      ea = nea;
+      eb = neb;
     }
-  };
+    return;
+  }
 
-  int b = blockIdx.x;
-  if (tid == 0 && b < nblk) issue(b, 0);
-  for (int it = 0; b < nblk; ++it, b += gridDim.x) {
-    const int st = it & 1;
-    if (tid == 0 && b + (int)gridDim.x < nblk) issue(b + gridDim.x, st ^ 1);
-    // this thread's row and its strip bounds: loaded before the wait so the
-    // latency overlaps the bulk copy
-    const long long row = (long long)b * kRowThreads + tid;
+  // ---------------- consumer warps
+  const int ctid = tid - 32;
+  const int lane = tid & 31;
+  const int q = ctid % T;          // segment index inside the row
+  const int rloc = ctid / T;       // row inside the block
+  // strip bounds of this thread's row, loaded one block ahead
+  int nsa = 0, nsb = 0;
+  if (RowCfg<DT>::kPrefetch && blockIdx.x < (unsigned)nblk) {
+    const long long row0 = (long long)blockIdx.x * kRowThreads + rloc;
+    if (row0 < rows) {
+      const int s0 = (int)(row0 / height);
+      nsa = sp[s0];
+      nsb = sp[s0 + 1];
+    }
+  }
+  for (int it = 0, b = blockIdx.x; b < nblk; ++it, b += gridDim.x) {
+    const int st = it % kRowStages, use = it / kRowStages;
+    const long long row = (long long)b * kRowThreads + rloc;
     const bool active = row < rows;
     const int s = active ? (int)(row / height) : 0;
     const uint32_t r = (uint32_t)(row - (long long)s * height);
-    const int sa = active ? sp[s] : 0, sb = active ? sp[s + 1] : 0;
-    const bool ok = mbar_wait_bounded(&bars[st], (it >> 1) & 1);
-    if (!ok) {
-      s_abort = 1;
-      atomicOr(status, ST_TIMEOUT);
+    int sa = nsa, sb = nsb;
+    if (!RowCfg<DT>::kPrefetch) {
+      sa = active ? sp[s] : 0;
+      sb = active ? sp[s + 1] : 0;
+    } else {
+      const long long rown = row + (long long)gridDim.x * kRowThreads;
+      if (rown < rows) {
+        const int sn = (int)(rown / height);
+        nsa = sp[sn];
+        nsb = sp[sn + 1];
+      }
     }
+    const bool ok = mbar_wait_bounded(&full[st], use & 1);
+    if (!ok) atomicOr(status, ST_TIMEOUT);
     const bool staged = info[st].staged;
     const char *stg = smem + st * stage_bytes;
     const uint32_t *cp = staged ? reinterpret_cast<const uint32_t *>(stg) : packed;
@@ -194,21 +281,34 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_row(int rows, int height, 
                                                        Stage<DT>::val_bytes(kRowCap))
                          : (Stage<DT>::kSplit ? lo : hi);
     const long long base = staged ? info[st].a8 : 0;
-    // row bounds: the first entry with RowInStrip >= r starts the row; the
-    // next row's start (held by the next lane when it is in the same strip)
-    // ends it
     const bool run = ok && active;
+    // the first lane of each row's group searches; the group shares the result
     int k0 = sa;
-    if (run && r > 0) k0 = lb_ris(cp, base, sa, sb, r, mask);
-    const int nxt = __shfl_down_sync(0xffffffffu, k0, 1);
+    if (run && r > 0 && q == 0) k0 = lb_ris(cp, base, sa, sb, r, mask);
+    if (T > 1) k0 = __shfl_sync(0xffffffffu, k0, lane & ~(T - 1));
+    const int nxt = __shfl_down_sync(0xffffffffu, k0, T);
     int k1 = sb;
     if (run && r + 1 < (uint32_t)height && row + 1 < rows) {
-      if ((tid & 31) < 31) k1 = nxt;
+      if (lane + T < 32) k1 = nxt;
       else k1 = lb_ris(cp, base, k0, sb, r + 1, mask);
     }
-    if (run) y[row] = row_dot<DT>(cp, vh, vl, base, k0, k1, bits, x);
-    __syncthreads();
-    if (s_abort) break;
+    A acc = A(0);
+    if (run) {
+      const int seg = (k1 - k0 + T - 1) / T;
+      const int a0 = min(k1, k0 + q * seg), a1 = min(k1, a0 + seg);
+      acc = seg_dot<DT, RowCfg<DT>::kCH, RowCfg<DT>::kILP>(cp, vh, vl, base, a0, a1, bits, x);
+    }
+    // join the T partial sums into lane q == 0 with T - 1 adds in total (FP64
+    // issue is counted per active lane, so only the lanes that keep a sum add)
+#pragma unroll
+    for (int o = T / 2; o >= 1; o >>= 1) {
+      const A other = __shfl_down_sync(0xffffffffu, acc, o);
+      if (q < o) acc += other;
+    }
+    if (run && q == 0) y[row] = acc;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if (!ok) break;
   }
 }
 
@@ -524,12 +624,12 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, int variant, char *ws
   const int sms = sm_count();
   if (variant == CMRS_VARIANT_ROW) {
     static Occ occ;
-    const size_t smem = kStages * Stage<DT>::bytes(kRowCap);
-    const int per_sm = occupancy(k_spmv_row<DT>, kRowThreads, smem, occ);
+    const size_t smem = kRowStages * Stage<DT>::bytes(kRowCap);
+    const int per_sm = occupancy(k_spmv_row<DT>, RowCfg<DT>::kThreads, smem, occ);
     const long long nblk = ceil_div(A->rows, kRowThreads);
     const int grid = (int)std::min<long long>(nblk, (long long)per_sm * sms);
-    k_spmv_row<DT><<<grid, kRowThreads, smem, st>>>(A->rows, A->height, A->bits, A->nnz, A->strip_ptr, A->col_packed,
-                                                    hi, lo, x, y, status);
+    k_spmv_row<DT><<<grid, RowCfg<DT>::kThreads, smem, st>>>(A->rows, A->height, A->bits, A->nnz, A->strip_ptr,
+                                                             A->col_packed, hi, lo, x, y, status);
     CMRS_LAUNCH_CHECK();
   } else if (variant == CMRS_VARIANT_STRIP) {
     static Occ occ;
