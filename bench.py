@@ -44,8 +44,11 @@ def args_parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--height", type=int, default=4)
-    p.add_argument("--variant", default="row", choices=["row", "strip", "merge"])
+    p.add_argument("--height", type=int, default=None, help="strip height (default: 4; power-law 32)")
+    p.add_argument("--variant", default=None, choices=["row", "strip", "merge"],
+                   help="SpMV kernel variant (default: row; power-law merge)")
+    p.add_argument("--workload", default="stencil27", choices=["stencil27", "powerlaw", "batched", "laplacian"],
+                   help="stencil27 is the headline; the others print the same JSON schema for their workload")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary storage-form measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
@@ -181,7 +184,17 @@ def run_reference(args):
         return
     import oracle
     from paper_1203_2946_gb300 import inputs
-    a, x = inputs.workload_stencil27_128()
+    if args.workload in ("stencil27", None):
+        a, x = inputs.workload_stencil27_128()
+        wl = "27-point stencil 128^3 (n=2097152, nnz=55742968), FP64, CRS order"
+    elif args.workload == "powerlaw":
+        a, x = inputs.workload_powerlaw_4m()
+        a = inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind, a.val.astype(np.float64))
+        x = x.astype(np.float64)
+        wl = "power-law rows n=4194304, FP32 values widened to FP64, CRS order"
+    else:
+        a, x = inputs.workload_laplacian_64()
+        wl = "5-point Laplacian 64x64, FP64, CRS order"
     h = args.height
     strips = (a.rows + h - 1) // h
     # each step is a bounded row slice of the workload, sized from one full call
@@ -209,8 +222,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / len(ts) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "27-point stencil 128^3 (n=2097152, nnz=55742968), FP64, CRS order; "
-                                   "each step a slice of %d rows" % nrow},
+            "config": {"workload": wl + "; each step a slice of %d rows" % nrow},
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": "%d consecutive rows per step (%.3f of the matrix), %d steps" % (
                                  nrow, nrow / a.rows, len(ts))},
@@ -391,10 +403,216 @@ def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
 
 def main():
     args = args_parse()
+    if args.height is None:
+        args.height = 32 if args.workload == "powerlaw" else 4
+    if args.variant is None:
+        args.variant = "merge" if args.workload == "powerlaw" else "row"
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "stencil27":
         run_ours(args)
+    else:
+        run_secondary(args)
+
+
+
+# --------------------------------------------------------------------------- secondary workloads
+def _line(args, metric_value, unit, per_ms, dtype, config, roofline, e2e, launches, clocks, extra=None):
+    line = {"metric": METRIC, "value": metric_value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config, "roofline": roofline,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if extra:
+        line.update(extra)
+    return line
+
+
+def run_secondary(args):
+    import torch
+    from paper_1203_2946_gb300 import build
+    build.build()
+    from paper_1203_2946_gb300 import binding as b, inputs
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peaks()
+    sampler = ClockSampler(None)
+    steps = args.steps
+    if args.workload in ("powerlaw", "laplacian"):
+        if args.workload == "powerlaw":
+            a, x = inputs.workload_powerlaw_4m()
+            dt, sv, name = b.CMRS_F32, 4, "f32"
+            wl = ("power-law rows, Zipf(2.1) clipped to [1,100000], n=4194304, nnz=%d (mean %.2f), "
+                  "FP32 values and x" % (a.nnz, a.nnz / a.rows))
+        else:
+            a, x = inputs.workload_laplacian_64()
+            dt, sv, name = b.CMRS_F64, 8, "f64"
+            wl = "5-point Laplacian 64x64 (n=4096, nnz=20224), FP64"
+        h, v = args.height, b.VARIANTS[args.variant]
+        rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
+        va = torch.from_numpy(np.ascontiguousarray(a.val)).to(dev)
+        M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=dt)
+        xd = torch.from_numpy(x).to(dev)
+        yd = torch.empty(a.rows, dtype=xd.dtype, device=dev)
+        ws = M.spmv_workspace(v)
+        fn = lambda: b.cmrs_spmv(M, xd, yd, v, ws)  # noqa: E731
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        with sampler:
+            times = time_steps(fn, steps, flush, stream)
+        per_ms = statistics.mean(times)
+        S = (a.rows + h - 1) // h
+        bp = beta_plus(a.nnz, a.rows, S, sv)
+        gbs = bp / (per_ms / 1e3) / 1e9
+        yref, scale = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val.astype(np.float64), x.astype(np.float64))
+        rel = np.abs(yd.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
+        extra = {"gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
+                 "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))},
+                 "cpu_baseline": cpu_oracle_rate(inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind,
+                                                            a.val.astype(np.float64)), x.astype(np.float64), S)}
+        if args.workload == "powerlaw":
+            forms = {}
+            for fname, fdt, fbp in (("bf16", b.CMRS_BF16, 6 * a.nnz + 4 * S + 8 * a.rows),):
+                F = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=fdt)
+                fws = F.spmv_workspace(v)
+                ff = lambda: b.cmrs_spmv(F, xd, yd, v, fws)  # noqa: E731
+                for _ in range(3):
+                    ff()
+                fms = statistics.mean(time_steps(ff, min(steps, 200), flush, stream))
+                frel = np.abs(yd.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
+                forms[fname] = {"gbs": fbp / (fms / 1e3) / 1e9, "ms": fms, "speedup_vs_f32": per_ms / fms,
+                                "err_vs_f64_oracle": {"max": float(frel.max()), "median": float(np.median(frel))}}
+            extra["forms"] = forms
+            var = {}
+            for vn, vv in b.VARIANTS.items():
+                vws = M.spmv_workspace(vv)
+                g = lambda: b.cmrs_spmv(M, xd, yd, vv, vws)  # noqa: E731
+                for _ in range(2):
+                    g()
+                vms = statistics.mean(time_steps(g, 20, flush, stream))
+                var[vn] = {"ms": vms, "gbs": bp / (vms / 1e3) / 1e9}
+            extra["variants_f32"] = var
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.empty(a.rows, dtype=xd.dtype).pin_memory()
+
+        def e2e():
+            xd.copy_(xh, non_blocking=True)
+            fn()
+            yh.copy_(yd, non_blocking=True)
+        for _ in range(3):
+            e2e()
+        e_ms = statistics.mean(time_steps(e2e, max(20, min(steps, 200)), flush, stream))
+        kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge"}[v]
+        line = _line(args, gbs, "GB/s", per_ms, name,
+                     {"workload": wl, "height": h, "variant": args.variant, "bytes_per_step": bp,
+                      "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
+                     {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                      "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": kname},
+                     {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(x.nbytes),
+                      "d2h_bytes_per_step": int(a.rows * x.itemsize), "ms_per_step": e_ms},
+                     steps * (3 if v == 2 else 1), sampler.summary(), extra)
+        print(json.dumps(line), flush=True)
+        return
+
+    # ---- batched: 256 banded-random matrices, k right-hand sides each
+    specs = inputs.batched_banded_specs()
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        mats_host = pool.map(_gen_batched, specs, chunksize=4)
+    h = args.height
+    mats, Xs, Ys, bp, nnz_total, rows_total = [], [], [], 0, 0, 0
+    for (rp_, ci_, val_, X_), sp_ in zip(mats_host, specs):
+        n = rp_.size - 1
+        rp, ci = torch.from_numpy(rp_).to(dev), torch.from_numpy(ci_).to(dev)
+        M = b.cmrs_from_csr(rp, ci, torch.from_numpy(val_).to(dev), n, h, dtype=b.CMRS_F32)
+        del rp, ci
+        mats.append(M)
+        Xs.append(torch.from_numpy(X_).to(dev))
+        Ys.append(torch.empty((n, X_.shape[1]), dtype=torch.float32, device=dev))
+        nnz = int(ci_.size)
+        bp += beta_plus(nnz, n, (n + h - 1) // h, 4) + 8 * (X_.shape[1] - 1) * n
+        nnz_total += nnz * X_.shape[1]
+        rows_total += n
+    best, _ = b.cmrs_spmm_autotune(mats, Xs, Ys, candidates=(2048, 8192, 32768, 131072), reps=3)
+    plan = b.SpmmPlan(mats, Xs, Ys, work_target=best, use_graph=True)
+    fn = lambda: b.cmrs_spmm_batched(plan)  # noqa: E731
+    for _ in range(max(3, args.warmup)):
+        fn()
+    torch.cuda.synchronize()
+    with sampler:
+        times = time_steps(fn, steps, flush, stream)
+    per_ms = statistics.mean(times)
+    gbs = bp / (per_ms / 1e3) / 1e9
+    # per-matrix plain launches of the same kernel, no graph
+    plain = lambda: [b.cmrs_spmm(M, X, Y) for M, X, Y in zip(mats, Xs, Ys)]  # noqa: E731
+    plain()
+    plain_ms = statistics.mean(time_steps(plain, 5, flush, stream))
+    # sampled parity against the oracle: 8 matrices, every column
+    worst = 0.0
+    for i in range(0, len(specs), len(specs) // 8):
+        rp_, ci_, val_, X_ = mats_host[i]
+        Y = Ys[i].cpu().numpy()
+        L = np.diff(rp_)
+        for c in range(X_.shape[1]):
+            yref, sc = oracle.csr_spmv(rp_, ci_, val_.astype(np.float64), X_[:, c].astype(np.float64))
+            err = np.abs(Y[:, c] - yref)
+            worst = max(worst, float(np.max(err / np.maximum((L + 2) * 2.0**-24 * sc, 1e-300))))
+    # plain FP64 CMRS SpMV, one launch per matrix and right-hand side (the baseline kernel)
+    f64_ms = None
+    sub = list(range(0, len(specs), 4))
+    mats64, cols64 = [], []
+    for i in sub:
+        rp_, ci_, val_, X_ = mats_host[i]
+        n = rp_.size - 1
+        M64 = b.cmrs_from_csr(torch.from_numpy(rp_).to(dev), torch.from_numpy(ci_).to(dev),
+                              torch.from_numpy(val_.astype(np.float64)).to(dev), n, h, dtype=b.CMRS_F64)
+        xs = [torch.from_numpy(np.ascontiguousarray(X_[:, c], dtype=np.float64)).to(dev) for c in range(X_.shape[1])]
+        mats64.append((M64, xs, torch.empty(n, dtype=torch.float64, device=dev), M64.spmv_workspace(0)))
+    f64 = lambda: [b.cmrs_spmv(M64, xc, y64, 0, w64) for M64, xs, y64, w64 in mats64 for xc in xs]  # noqa: E731
+    f64()
+    f64_sub_ms = statistics.mean(time_steps(f64, 3, flush, stream))
+    plain_sub = lambda: [b.cmrs_spmm(mats[i], Xs[i], Ys[i]) for i in sub]  # noqa: E731
+    plain_sub()
+    plain_sub_ms = statistics.mean(time_steps(plain_sub, 3, flush, stream))
+    Xh = [X.cpu().pin_memory() for X in Xs]
+    Yh = [torch.empty_like(Y, device="cpu").pin_memory() for Y in Ys]
+
+    def e2e():
+        for X, H in zip(Xs, Xh):
+            X.copy_(H, non_blocking=True)
+        fn()
+        for Y, H in zip(Ys, Yh):
+            H.copy_(Y, non_blocking=True)
+    e2e()
+    e_ms = statistics.mean(time_steps(e2e, 5, flush, stream))
+    info = plan.info()
+    line = _line(args, gbs, "GB/s", per_ms, "f32",
+                 {"workload": "256 banded-random matrices (n~U[1000,200000], bandwidth~U[64,2048], 10-60 nnz/row, "
+                              "k in {1,4,8,32}), FP32, CMRS h=%d; one persistent graph-replayed launch" % h,
+                  "matrices": len(specs), "rows_total": rows_total, "entry_columns": nnz_total,
+                  "bytes_per_step": bp, "schedule": {"work_target": best, **info},
+                  "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
+                 {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                  "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmm_queue"},
+                 {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s",
+                  "h2d_bytes_per_step": int(sum(X.numel() for X in Xs) * 4),
+                  "d2h_bytes_per_step": int(sum(Y.numel() for Y in Ys) * 4), "ms_per_step": e_ms},
+                 steps, sampler.summary(),
+                 {"gflops": 2 * nnz_total / (per_ms / 1e3) / 1e9,
+                  "per_matrix_launches": {"ms": plain_ms, "speedup_of_batched": plain_ms / per_ms},
+                  "plain_f64_spmv_per_column": {"matrices": len(sub), "ms": f64_sub_ms,
+                                                "batched_f32_ms_same_subset": plain_sub_ms,
+                                                "speedup_of_f32_spmm": f64_sub_ms / plain_sub_ms},
+                  "parity_sample": {"matrices": 8, "max_err_over_tolerance": worst}})
+    print(json.dumps(line), flush=True)
+
+
+def _gen_batched(spec):
+    from paper_1203_2946_gb300 import inputs
+    a, X = inputs.batched_banded(spec)
+    return a.row_ptr, a.col_ind, a.val, X
 
 
 if __name__ == "__main__":

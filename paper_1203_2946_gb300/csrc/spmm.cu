@@ -22,6 +22,7 @@ namespace cmrs {
 namespace {
 
 constexpr int kSpmmThreads = 256;
+constexpr int kSpmmCH = 8;  // entries whose gathers are in flight together
 
 struct Desc {
   int32_t rows, height, bits, k;
@@ -77,19 +78,22 @@ __device__ __forceinline__ void spmm_rows(const Desc &d, int row0, int row1, int
     for (int c0 = 0; c0 < k; c0 += G) {
       const int col = c0 + g;
       if (active && col < k) {
+        // kSpmmCH entries per batch: their column words, values and X gathers
+        // are all issued before the FMAs that use them
         float acc = 0.f;
-        int j = k0;
-        for (; j + 2 <= k1; j += 2) {
-          const uint32_t p0 = __ldg(d.packed + j), p1 = __ldg(d.packed + j + 1);
-          const float v0 = __ldg(d.val + j), v1 = __ldg(d.val + j + 1);
-          const float x0 = __ldg(d.X + (size_t)(p0 >> d.bits) * k + col);
-          const float x1 = __ldg(d.X + (size_t)(p1 >> d.bits) * k + col);
-          acc = fmaf(v0, x0, acc);
-          acc = fmaf(v1, x1, acc);
-        }
-        if (j < k1) {
-          const uint32_t p0 = __ldg(d.packed + j);
-          acc = fmaf(__ldg(d.val + j), __ldg(d.X + (size_t)(p0 >> d.bits) * k + col), acc);
+        for (int j = k0; j < k1; j += kSpmmCH) {
+          float xv[kSpmmCH], vv[kSpmmCH];
+#pragma unroll
+          for (int u = 0; u < kSpmmCH; ++u) {
+            if (j + u < k1) {
+              const uint32_t p = __ldg(d.packed + j + u);
+              vv[u] = __ldg(d.val + j + u);
+              xv[u] = __ldg(d.X + (size_t)(p >> d.bits) * k + col);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kSpmmCH; ++u)
+            if (j + u < k1) acc = fmaf(vv[u], xv[u], acc);
         }
         d.Y[(size_t)row * k + col] = acc;
       }

@@ -341,3 +341,10 @@ def selector_matrix(spec) -> CSR:
         kmax = int(min(n // 4, 20 * spec["mu"] * 50))
         return powerlaw_rows(n, spec["alpha"], max(kmax, 2), seed)
     return uniform_random(n, spec["mu"], seed)
+
+
+def selector_matrix_arrays(spec):
+    """selector_matrix as plain arrays (rows, cols, row_ptr, col_ind, FP32
+    values), for worker processes."""
+    a = selector_matrix(spec)
+    return a.rows, a.cols, a.row_ptr, a.col_ind, np.ascontiguousarray(a.val, dtype=np.float32)

@@ -78,11 +78,6 @@ def time_all_choices(a: inputs.CSR, timer: Timer, device, reps=5):
     return feat, out
 
 
-def _gen(spec):
-    a = inputs.selector_matrix(spec)
-    return a.rows, a.cols, a.row_ptr, a.col_ind, np.ascontiguousarray(a.val, dtype=np.float32)
-
-
 def build_corpus(specs, device="cuda", reps=5, workers=None, log=None):
     """Features and exhaustive timings for every spec.  Matrices are generated
     on host processes started with `spawn` (safe next to a CUDA context)."""
@@ -91,7 +86,7 @@ def build_corpus(specs, device="cuda", reps=5, workers=None, log=None):
     workers = workers or max(1, min(12, (os.cpu_count() or 2) - 2))
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        for i, (rows, cols, rp, ci, val) in enumerate(pool.imap(_gen, specs, chunksize=2)):
+        for i, (rows, cols, rp, ci, val) in enumerate(pool.imap(inputs.selector_matrix_arrays, specs, chunksize=2)):
             a = inputs.CSR(rows, cols, rp, ci, val)
             f, t = time_all_choices(a, timer, device, reps)
             feats.append(f)
