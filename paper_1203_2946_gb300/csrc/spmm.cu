@@ -22,7 +22,7 @@ namespace cmrs {
 namespace {
 
 constexpr int kSpmmThreads = 256;
-constexpr int kSpmmCH = 8;  // entries whose gathers are in flight together
+constexpr int kSpmmCH = 2;  // entries whose gathers are in flight together (8 raised registers to 64 and was slower)
 
 struct Desc {
   int32_t rows, height, bits, k;

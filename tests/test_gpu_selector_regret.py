@@ -1,0 +1,57 @@
+"""The learned strip selector against the exhaustive sweep it replaces.
+
+The committed corpus (paper_1203_2946_gb300/data/selector_corpus.npz) holds
+the exhaustive timings (6 heights x 3 variants) of 2,000 seeded matrices on a
+GB300, produced by build_selector.py.  Here the network is retrained from
+scratch with the library's own forward/backward/Adam kernels and judged on
+the 500 held-out matrices: its regret t(choice)/t(best) must stay within 10%
+(geometric mean) and beat the method without it -- the fixed default h = 4,
+ROW, and the best single fixed choice picked on the training matrices."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+DATA = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1203_2946_gb300", "data")
+
+
+@pytest.fixture(scope="module")
+def corpus():
+    from paper_1203_2946_gb300 import build
+    build.build()
+    d = np.load(os.path.join(DATA, "selector_corpus.npz"))
+    return d["features"], d["times"]
+
+
+def test_retrained_network_regret_on_held_out(corpus):
+    from paper_1203_2946_gb300 import selector
+    feats, times = corpus
+    assert feats.shape == (2000, 24) and times.shape == (2000, 18)
+    tr, te = selector.split(len(times), 500, seed=0)
+    model = selector.train(feats, times, tr, steps=4000)
+    net = selector.regret(times[te], selector.predict(model, feats[te]))
+    default = selector.regret(times[te], np.full(len(te), 3 * selector.HEIGHTS.index(4)))
+    fixed = int(np.argmin(np.exp(np.mean(np.log(times[tr] / times[tr].min(1, keepdims=True)), axis=0))))
+    single = selector.regret(times[te], np.full(len(te), fixed))
+    assert net["geomean"] <= 1.10, net
+    assert net["geomean"] < default["geomean"] and net["geomean"] < single["geomean"]
+    assert net["median"] <= 1.01
+
+
+def test_committed_model_through_select_strip(corpus):
+    from paper_1203_2946_gb300 import binding as b, inputs, selector
+    model = selector.load_model(os.path.join(DATA, "selector_model.npz"))
+    feats, times = corpus
+    tr, te = selector.split(len(times), 500, seed=0)
+    assert selector.regret(times[te], selector.predict(model, feats[te]))["geomean"] <= 1.10
+    # the device path (features, normalisation, network, argmin in libcmrs)
+    # picks a valid choice and agrees with the host-side prediction
+    a = inputs.banded_random(50000, 700, 10, 60, seed=12)
+    rp, ci = torch.from_numpy(a.row_ptr).cuda(), torch.from_numpy(a.col_ind).cuda()
+    h, v = b.cmrs_select_strip(rp, ci, a.cols, model)
+    f = b.cmrs_features(rp, ci).cpu().numpy()[None, :]
+    c = int(selector.predict(model, f)[0])
+    assert (h, v) == (b.SEL_HEIGHTS[c // 3], c % 3)
