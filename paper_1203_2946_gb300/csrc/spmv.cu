@@ -120,8 +120,14 @@ __device__ __forceinline__ int lb_ris(const uint32_t *cp, long long base, int lo
 #endif
 constexpr int kRowStages = CMRS_ROW_STAGES;
 
+// x gathers a thread issues per batch; 0 = a 32-entry row share.  FP64 uses 7,
+// a 27-point row's share at T = 4 (measured 173 -> 164 us on the 27-point
+// 128^3 matrix against 8).
 #ifndef CMRS_ROW_CH
 #define CMRS_ROW_CH 0
+#endif
+#ifndef CMRS_ROW_CH_F64
+#define CMRS_ROW_CH_F64 7
 #endif
 #ifndef CMRS_ROW_ILP
 #define CMRS_ROW_ILP 1
@@ -142,7 +148,8 @@ struct RowCfg {
   static constexpr int kConsumers = kRowThreads * T;   // threads
   static constexpr int kThreads = kConsumers + 32;     // + producer warp
   // x gathers a thread issues per batch (default: a whole 32-entry row share)
-  static constexpr int kCH = CMRS_ROW_CH > 0 ? CMRS_ROW_CH : ((32 / T) < 8 ? 8 : (32 / T));
+  static constexpr int kCH = (DT == CMRS_F64 && CMRS_ROW_CH_F64 > 0) ? CMRS_ROW_CH_F64
+                             : CMRS_ROW_CH > 0 ? CMRS_ROW_CH : ((32 / T) < 8 ? 8 : (32 / T));
   static constexpr int kILP = CMRS_ROW_ILP;            // independent FMA chains per segment
   static constexpr bool kPrefetch = DT == CMRS_F64 ? CMRS_ROW_PREFETCH_F64 : CMRS_ROW_PREFETCH_F32;
 };
@@ -161,14 +168,20 @@ __device__ __forceinline__ typename Form<DT>::Acc seg_dot(const uint32_t *cp, co
   A acc[ILP];
 #pragma unroll
   for (int i = 0; i < ILP; ++i) acc[i] = A(0);
-  for (int k = lo; k < hi; k += CH) {
+  // longest segment in the warp: FMAs past it are not issued at all (FP64
+  // issue is charged per warp instruction, whatever its active lanes)
+  const int nmax = __reduce_max_sync(0xffffffffu, hi - lo);
+  for (int j0 = 0; j0 < nmax; j0 += CH) {
+    const int k = lo + j0;
     A xv[CH];
 #pragma unroll
     for (int j = 0; j < CH; ++j)
       if (k + j < hi) xv[j] = ld_x(x + (cp[k + j - base] >> bits));
 #pragma unroll
     for (int j = 0; j < CH; ++j)
-      if (k + j < hi) acc[j % ILP] = fma_acc(Form<DT>::value(vh, vl, k + j - base), xv[j], acc[j % ILP]);
+      if (j0 + j < nmax) {  // warp-uniform
+        if (k + j < hi) acc[j % ILP] = fma_acc(Form<DT>::value(vh, vl, k + j - base), xv[j], acc[j % ILP]);
+      }
   }
 #pragma unroll
   for (int i = 1; i < ILP; ++i) acc[0] += acc[i];
@@ -292,12 +305,11 @@ __global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int
       if (lane + T < 32) k1 = nxt;
       else k1 = lb_ris(cp, base, k0, sb, r + 1, mask);
     }
-    A acc = A(0);
-    if (run) {
-      const int seg = (k1 - k0 + T - 1) / T;
-      const int a0 = min(k1, k0 + q * seg), a1 = min(k1, a0 + seg);
-      acc = seg_dot<DT, RowCfg<DT>::kCH, RowCfg<DT>::kILP>(cp, vh, vl, base, a0, a1, bits, x);
-    }
+    // every lane calls (an inactive row has an empty segment) so that the
+    // warp-wide bound inside is well defined
+    const int seg = run ? (k1 - k0 + T - 1) / T : 0;
+    const int a0 = run ? min(k1, k0 + q * seg) : 0, a1 = run ? min(k1, a0 + seg) : 0;
+    A acc = seg_dot<DT, RowCfg<DT>::kCH, RowCfg<DT>::kILP>(cp, vh, vl, base, a0, a1, bits, x);
     // join the T partial sums into lane q == 0 with T - 1 adds in total (FP64
     // issue is counted per active lane, so only the lanes that keep a sum add)
 #pragma unroll
