@@ -351,6 +351,8 @@ def run_ours(args):
     if rank == 0 and not args.no_extras and world == 1:
         line["forms"] = storage_forms(b, a, x, rp, ci, va, h, flush, stream, per_ms)
         line["variants_f64"] = variant_sweep(b, a, xd, M, flush, stream, bp)
+        line["heights_f64_row"] = height_sweep(b, a, xd, rp, ci, va, flush, stream)
+        line["conversion"] = conversion_times(b, a, rp, ci, va, M, h)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(a, x, strips)
     if rank == 0:
@@ -385,6 +387,49 @@ def storage_forms(b, a, x, rp, ci, va, h, flush, stream, f64_ms, steps=200):
         out[name] = {"gbs": bp / (ms / 1e3) / 1e9, "ms": ms, "speedup_vs_f64": f64_ms / ms,
                      "gflops": 2 * a.nnz / (ms / 1e3) / 1e9,
                      "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))}}
+        del M
+    return out
+
+
+def conversion_times(b, a, rp, ci, va, M, h, reps=5):
+    """CRS -> CMRS (plain and strip-sorted) and CMRS -> CRS on the same matrix:
+    median wall time of `reps` calls (each call synchronises once), and GB/s
+    over the arrays read and written (24 B per entry + the pointer arrays)."""
+    import torch
+
+    def tm(fn):
+        ts = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts[1:]) * 1e3
+    S = (a.rows + h - 1) // h
+    moved = 24 * a.nnz + 4 * (a.rows + 1) + 4 * (S + 1)
+    out = {}
+    for name, flags in (("from_csr_f64", 0), ("from_csr_f64_sorted", b.CMRS_SORTED)):
+        ms = tm(lambda: b.cmrs_from_csr(rp, ci, va, a.cols, h, flags=flags, dtype=b.CMRS_F64))
+        out[name] = {"ms": ms, "gbs": moved / (ms / 1e3) / 1e9}
+    ms = tm(lambda: b.cmrs_to_csr(M))
+    out["to_csr_f64"] = {"ms": ms, "gbs": moved / (ms / 1e3) / 1e9}
+    out["note"] = "includes the binding's output allocations and one status read-back per call"
+    return out
+
+
+def height_sweep(b, a, xd, rp, ci, va, flush, stream, steps=60):
+    import torch
+    out = {}
+    y = torch.empty(a.rows, dtype=torch.float64, device=xd.device)
+    for h in (1, 2, 4, 8, 16, 32):
+        M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F64)
+        ws = M.spmv_workspace(0)
+        for _ in range(3):
+            b.cmrs_spmv(M, xd, y, 0, ws)
+        ms = statistics.mean(time_steps(lambda: b.cmrs_spmv(M, xd, y, 0, ws), steps, flush, stream))
+        S = (a.rows + h - 1) // h
+        out["h%d" % h] = {"ms": ms, "gbs": beta_plus(a.nnz, a.rows, S, 8) / (ms / 1e3) / 1e9}
         del M
     return out
 
