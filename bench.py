@@ -44,10 +44,11 @@ def args_parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--height", type=int, default=None, help="strip height (default: 4; power-law 32)")
-    p.add_argument("--variant", default=None, choices=["row", "strip", "merge"],
-                   help="SpMV kernel variant (default: row; power-law merge)")
-    p.add_argument("--workload", default="stencil27", choices=["stencil27", "powerlaw", "batched", "laplacian"],
+    p.add_argument("--height", type=int, default=None, help="strip height (default: 4; power-law and p7 32)")
+    p.add_argument("--variant", default=None, choices=["row", "strip", "merge", "auto"],
+                   help="SpMV kernel variant (default: row; power-law merge; p7 and dense4 auto)")
+    p.add_argument("--workload", default="stencil27",
+                   choices=["stencil27", "powerlaw", "batched", "laplacian", "p7", "dense4"],
                    help="stencil27 is the headline; the others print the same JSON schema for their workload")
     p.add_argument("--batch-count", type=int, default=256, help="batched workload: matrices (256 = full size)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary storage-form measurements")
@@ -450,9 +451,9 @@ def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
 def main():
     args = args_parse()
     if args.height is None:
-        args.height = 32 if args.workload == "powerlaw" else 4
+        args.height = 32 if args.workload in ("powerlaw", "p7") else 4
     if args.variant is None:
-        args.variant = "merge" if args.workload == "powerlaw" else "row"
+        args.variant = {"powerlaw": "merge", "p7": "auto", "dense4": "auto"}.get(args.workload, "row")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stencil27":
@@ -485,8 +486,18 @@ def run_secondary(args):
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(None)
     steps = args.steps
-    if args.workload in ("powerlaw", "laplacian"):
-        if args.workload == "powerlaw":
+    if args.workload in ("powerlaw", "laplacian", "p7", "dense4"):
+        if args.workload == "p7":
+            a = inputs.permutation_matrix()
+            x = inputs.uniform_vector(a.cols, 0)
+            dt, sv, name = b.CMRS_F64, 8, "f64"
+            wl = "p7: 10^7 x 10^7 random permutation (one entry per row), FP64"
+        elif args.workload == "dense4":
+            a = inputs.dense_as_sparse()
+            x = inputs.uniform_vector(a.cols, 0)
+            dt, sv, name = b.CMRS_F64, 8, "f64"
+            wl = "dense4: 10^4 x 10^4 dense matrix stored as sparse (nnz = 10^8), FP64"
+        elif args.workload == "powerlaw":
             a, x = inputs.workload_powerlaw_4m()
             dt, sv, name = b.CMRS_F32, 4, "f32"
             wl = ("power-law rows, Zipf(2.1) clipped to [1,100000], n=4194304, nnz=%d (mean %.2f), "
@@ -495,10 +506,11 @@ def run_secondary(args):
             a, x = inputs.workload_laplacian_64()
             dt, sv, name = b.CMRS_F64, 8, "f64"
             wl = "5-point Laplacian 64x64 (n=4096, nnz=20224), FP64"
-        h, v = args.height, b.VARIANTS[args.variant]
+        h, v = args.height, dict(b.VARIANTS, auto=b.CMRS_VARIANT_AUTO)[args.variant]
         rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
         va = torch.from_numpy(np.ascontiguousarray(a.val)).to(dev)
         M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=dt)
+        ran = b.cmrs_spmv_variant(M, v)
         xd = torch.from_numpy(x).to(dev)
         yd = torch.empty(a.rows, dtype=xd.dtype, device=dev)
         ws = M.spmv_workspace(v)
@@ -515,9 +527,21 @@ def run_secondary(args):
         yref, scale = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val.astype(np.float64), x.astype(np.float64))
         rel = np.abs(yd.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
         extra = {"gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
-                 "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))},
-                 "cpu_baseline": cpu_oracle_rate(inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind,
-                                                            a.val.astype(np.float64)), x.astype(np.float64), S)}
+                 "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))}}
+        if not args.no_cpu:
+            extra["cpu_baseline"] = cpu_oracle_rate(inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind,
+                                                               a.val.astype(np.float64)), x.astype(np.float64), S)
+        if args.workload in ("p7", "dense4"):
+            var = {}
+            for vn, vv in b.VARIANTS.items():
+                vws = M.spmv_workspace(vv)
+                g = lambda: b.cmrs_spmv(M, xd, yd, vv, vws)  # noqa: E731
+                for _ in range(2):
+                    g()
+                vms = statistics.mean(time_steps(g, 20, flush, stream))
+                var[vn] = {"ms": vms, "gbs": bp / (vms / 1e3) / 1e9}
+            extra["variants_f64"] = var
+            fn()
         if args.workload == "powerlaw":
             forms = {}
             for fname, fdt, fbp in (("bf16", b.CMRS_BF16, 6 * a.nnz + 4 * S + 8 * a.rows),):
@@ -550,15 +574,16 @@ def run_secondary(args):
         for _ in range(3):
             e2e()
         e_ms = statistics.mean(time_steps(e2e, max(20, min(steps, 200)), flush, stream))
-        kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge"}[v]
+        kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge"}[ran]
         line = _line(args, gbs, "GB/s", per_ms, name,
-                     {"workload": wl, "height": h, "variant": args.variant, "bytes_per_step": bp,
+                     {"workload": wl, "height": h, "variant": args.variant,
+                      "kernel_variant": ("row", "strip", "merge")[ran], "bytes_per_step": bp,
                       "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
                      {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                       "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": kname},
                      {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(x.nbytes),
                       "d2h_bytes_per_step": int(a.rows * x.itemsize), "ms_per_step": e_ms},
-                     steps * (3 if v == 2 else 1), sampler.summary(), extra)
+                     steps * (3 if ran == 2 else 1), sampler.summary(), extra)
         print(json.dumps(line), flush=True)
         return
 

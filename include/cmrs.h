@@ -66,9 +66,10 @@ extern "C" {
 /* ---- SpMV kernel variants -------------------------------------------------
  * Every variant computes the same y = A x; they differ in how threads are
  * mapped onto strips (Section 4 gives one warp per strip).
- *   CMRS_VARIANT_ROW    one thread per row; a CTA stages the strips of 128
- *                       consecutive rows into shared memory with bulk async
- *                       copies and each thread walks its row there.  Needs
+ *   CMRS_VARIANT_ROW    a few threads per row (4 for CMRS_F64, 2 for the
+ *                       other forms), each summing a contiguous share of the
+ *                       row; a CTA stages the strips of 128 consecutive rows
+ *                       into shared memory with bulk async copies.  Needs
  *                       unsorted strips.  Best for regular rows.
  *   CMRS_VARIANT_STRIP  Algorithm 1 of Section 4: one warp per strip, lanes
  *                       stride through the strip and accumulate per-row
@@ -78,7 +79,11 @@ extern "C" {
  *                       of consecutive entries, rows that cross thread or
  *                       tile boundaries are joined afterwards in a fixed
  *                       order.  Needs unsorted strips.  Best for skewed rows.
- *   CMRS_VARIANT_AUTO   (-1) ROW, or STRIP for sorted strips. */
+ *   CMRS_VARIANT_AUTO   (-1) STRIP for sorted strips.  Otherwise, with
+ *                       mu = nnz / rows: MERGE if mu < 2, mu > 32, or
+ *                       max_strip_nnz > 8 * height * mu (or unknown, -1);
+ *                       ROW for the rest.  cmrs_spmv_variant reports the
+ *                       choice. */
 #define CMRS_VARIANT_AUTO (-1)
 #define CMRS_VARIANT_ROW 0
 #define CMRS_VARIANT_STRIP 1
@@ -164,6 +169,13 @@ int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *col_ind_out
  * (fixed summation order, no atomics on values): repeated calls give
  * bit-identical y. */
 int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes);
+
+/* The kernel variant cmrs_spmv runs for `variant` (resolves
+ * CMRS_VARIANT_AUTO by the rule above; checks that an explicit variant suits
+ * the matrix).  *resolved receives CMRS_VARIANT_ROW, _STRIP or _MERGE.  Host
+ * only: reads the fields of *A, never its device arrays.  Errors as
+ * cmrs_spmv_workspace (CMRS_ERR_UNSUPPORTED: ROW or MERGE on sorted strips). */
+int cmrs_spmv_variant(const cmrs_matrix *A, int variant, int *resolved);
 int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant,
               void *workspace, size_t workspace_bytes, void *stream);
 

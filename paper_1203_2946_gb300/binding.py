@@ -73,6 +73,7 @@ def lib():
             "cmrs_to_csr_workspace": ([M, ctypes.POINTER(sz)], i),
             "cmrs_to_csr": ([M, vp, vp, vp, vp, sz, vp], i),
             "cmrs_spmv_workspace": ([M, i, ctypes.POINTER(sz)], i),
+            "cmrs_spmv_variant": ([M, i, ctypes.POINTER(ctypes.c_int)], i),
             "cmrs_spmv": ([M, vp, vp, i, vp, sz, vp], i),
             "cmrs_spmv_check": ([M, i, vp, vp], i),
             "cmrs_spmv_noalloc": ([M, vp, vp, vp], i),
@@ -208,6 +209,13 @@ def cmrs_spmv(A: Matrix, x, y=None, variant=CMRS_VARIANT_AUTO, workspace_tensor=
     rc = lib().cmrs_spmv(A.ref(), _ptr(x), _ptr(y), variant, _ptr(ws), ws.numel(), _stream(stream))
     _check(rc, "cmrs_spmv")
     return y
+
+
+def cmrs_spmv_variant(A: Matrix, variant=CMRS_VARIANT_AUTO):
+    """The kernel variant (CMRS_VARIANT_ROW/_STRIP/_MERGE) cmrs_spmv runs."""
+    out = ctypes.c_int(-1)
+    _check(lib().cmrs_spmv_variant(A.ref(), variant, ctypes.byref(out)), "cmrs_spmv_variant")
+    return out.value
 
 
 def cmrs_spmv_noalloc(A: Matrix, x, y=None, stream=None):

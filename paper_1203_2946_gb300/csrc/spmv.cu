@@ -25,6 +25,7 @@ constexpr int kRowCap = 32 * CMRS_ROW_ROWS;   // ROW: entries per shared-memory 
 constexpr int kMergeThreads = 128;
 constexpr int kMergeE = 15;  // MERGE: entries per thread; odd, so that a warp's shared loads hit 32 banks
 constexpr int kMergeTile = kMergeThreads * kMergeE;
+constexpr int kMergeWarps = kMergeThreads / 32;
 constexpr int kStripWarps = 8;
 constexpr int kStages = 2;
 
@@ -406,11 +407,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_spmv_merge(int rows, int heig
   extern __shared__ __align__(128) char smem[];
   __shared__ uint64_t bars[kStages];
   __shared__ StageInfo info[kStages];
-  __shared__ A s_head[kMergeThreads], s_tail[kMergeThreads];
-  __shared__ int s_hrow[kMergeThreads], s_trow[kMergeThreads];
-  __shared__ uint8_t s_flag[kMergeThreads];
-  __shared__ int s_abort;
-  const int tid = threadIdx.x;
+  __shared__ A s_wv[kMergeWarps];         // per warp: scan value of its last lane
+  __shared__ int s_wf[kMergeWarps];       // per warp: a segment starts in it
+  __shared__ unsigned s_wt[kMergeWarps];  // per warp: lanes whose single run passes through
+  __shared__ int s_head0, s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t mask = (1u << bits) - 1;
   const size_t stage_bytes = Stage<DT>::bytes(kMergeTile);
   if (tid == 0) {
@@ -449,6 +450,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_spmv_merge(int rows, int heig
     const long long k0 = ta + (long long)tid * kMergeE;
     const long long k1 = min(k0 + kMergeE, tb);
     uint8_t flags = 0;
+    A hv = A(0), tv = A(0);      // head partial (row continued from before), tail partial (row going on)
+    uint32_t hrow = 0, trow = 0;
+    // lanes with entries in this tile (every lane of the warp votes)
+    const unsigned part = __ballot_sync(0xffffffffu, ok && k0 < tb);
     if (ok && k0 < tb) {
       // strip holding k0: the largest s in [s_lo, s_hi] with StripPtr[s] <= k0
       int slo = tile_strip[t];
@@ -466,51 +471,58 @@ __global__ void __launch_bounds__(kMergeThreads) k_spmv_merge(int rows, int heig
         const uint32_t cprev = k0 > ta ? cp[k0 - 1 - base] : __ldg(packed + k0 - 1);
         cont_in = (cprev & mask) == (cp[k0 - base] & mask);
       }
+      const int n = (int)(k1 - k0);  // 1 .. kMergeE
       // operands first, so that the x loads of the run are in flight together
       uint32_t c[kMergeE];
       A xv[kMergeE], v[kMergeE];
 #pragma unroll
       for (int j = 0; j < kMergeE; ++j) {
-        if (k0 + j < k1) {
+        if (j < n) {
           const long long i = k0 + j - base;
           c[j] = cp[i];
           v[j] = Form<DT>::value(vh, vl, i);
           xv[j] = ld_x(x + (c[j] >> bits));
         }
       }
-      long long run_row = -1;
-      A acc = A(0), head_sum = A(0);
-      int nruns = 0;
-      long long head_row = -1;
-      if (k0 == 0) {
-        // rows before the first entry of the matrix are empty
-        while (k0 >= next) next = sp[++cur + 1];
-        const long long r0 = (long long)cur * height + (c[0] & mask);
-        for (long long g = 0; g < r0 && g < rows; ++g) y[g] = A(0);
-      }
+      // row of every entry: integer work only (the strip walk may diverge)
+      uint32_t rw[kMergeE];
 #pragma unroll
       for (int j = 0; j < kMergeE; ++j) {
-        if (k0 + j < k1) {
-          const long long k = k0 + j;
-          while (k >= next) next = sp[++cur + 1];
-          const long long row = (long long)cur * height + (c[j] & mask);
-          if (row != run_row) {
-            if (run_row >= 0) {
-              if (nruns == 1 && cont_in) {
-                head_sum = acc;
-                head_row = run_row;
-              } else if (run_row < rows) {
-                y[run_row] = acc;
-              }
-              for (long long g = run_row + 1; g < row && g < rows; ++g) y[g] = A(0);
-            }
-            run_row = row;
-            acc = A(0);
-            ++nruns;
-          }
-          acc = fma_acc(v[j], xv[j], acc);
+        if (j < n) {
+          while (k0 + j >= next) next = sp[++cur + 1];
+          rw[j] = (uint32_t)cur * (uint32_t)height + (c[j] & mask);
         }
       }
+      // rows before the first entry of the matrix are empty
+      if (k0 == 0)
+        for (uint32_t g = 0; g < rw[0] && g < (uint32_t)rows; ++g) y[g] = A(0);
+      // The sums: one FMA chain per run of equal rows, no branch around the
+      // FMAs (a finished run leaves by a predicated store or a select), and
+      // the warp reconverged first, so that every FMA issues for the whole
+      // warp (FP64 issue is charged per warp instruction).
+      __syncwarp(part);
+      A acc = fma_acc(v[0], xv[0], A(0));
+      A head_sum = A(0);
+      bool first = true;  // the current run is this thread's first
+      uint32_t run_row = rw[0];
+#pragma unroll
+      for (int j = 1; j < kMergeE; ++j) {
+        if (j < n) {
+          const bool nw = rw[j] != rw[j - 1];
+          const bool to_head = nw && first && cont_in;  // first run continues a row from before k0
+          head_sum = to_head ? acc : head_sum;
+          if (nw && !to_head && rw[j - 1] < (uint32_t)rows) y[rw[j - 1]] = acc;
+          first = first && !nw;
+          acc = nw ? A(0) : acc;
+          acc = fma_acc(v[j], xv[j], acc);
+          run_row = rw[j];
+        }
+      }
+      // rows with no entries between two runs of this thread
+#pragma unroll
+      for (int j = 1; j < kMergeE; ++j)
+        if (j < n)
+          for (uint32_t g = rw[j - 1] + 1; g < rw[j] && g < (uint32_t)rows; ++g) y[g] = A(0);
       // the entry after this thread's last one: same row?
       long long next_row = rows;
       if (k1 < nnz) {
@@ -519,66 +531,107 @@ __global__ void __launch_bounds__(kMergeThreads) k_spmv_merge(int rows, int heig
         while (k1 >= sp[s2 + 1]) ++s2;
         next_row = (long long)s2 * height + (cn & mask);
       }
-      const bool cont_out = next_row == run_row;
-      if (nruns == 1 && cont_in) {
-        s_head[tid] = acc;
-        s_hrow[tid] = (int)run_row;
+      const bool cont_out = next_row == (long long)run_row;
+      if (first && cont_in) {
+        // one run, continuing a row from before k0
+        hv = acc;
+        hrow = run_row;
         flags = cont_out ? (F_HEAD | F_THROUGH) : F_HEAD;
       } else {
-        if (head_row >= 0) {
-          s_head[tid] = head_sum;
-          s_hrow[tid] = (int)head_row;
+        if (cont_in) {
+          hv = head_sum;
+          hrow = rw[0];
           flags = F_HEAD;
         }
         if (cont_out) {
-          s_tail[tid] = acc;
-          s_trow[tid] = (int)run_row;
+          tv = acc;
+          trow = run_row;
           flags |= F_TAIL;
-        } else if (run_row < rows) {
+        } else if (run_row < (uint32_t)rows) {
           y[run_row] = acc;
         }
       }
       if (!cont_out)
-        for (long long g = run_row + 1; g < next_row && g < rows; ++g) y[g] = A(0);
+        for (long long g = (long long)run_row + 1; g < next_row && g < rows; ++g) y[g] = A(0);
     }
-    s_flag[tid] = flags;
+    // Rows crossing thread boundaries, joined by a segmented scan over the
+    // tile's threads in thread order.  A thread whose single run continues on
+    // both sides (THROUGH) passes its head partial along; every other thread
+    // starts a segment with its tail partial (0 if none).  A row that ends
+    // inside thread e (HEAD, not THROUGH) is the segment's running sum at
+    // e - 1 plus e's head partial.  The in-warp scan takes as many shuffle
+    // steps as the longest run of THROUGH lanes needs (0..5, warp-uniform), so
+    // short rows pay nothing and a tile inside one long row pays 5 FP64 adds
+    // per warp instead of a 127-step serial walk.
+    const bool through = (flags & F_THROUGH) != 0;
+    const bool start = !through || tid == 0;
+    A v = through ? hv : ((flags & F_TAIL) ? tv : A(0));
+    bool f = start;
+    unsigned z = ~__ballot_sync(0xffffffffu, start);
+    int nsteps = 0;  // ceil(log2(longest run of non-start lanes + 1))
+    for (int sh = 1; sh <= 16 && z; sh <<= 1) {
+      ++nsteps;
+      z &= z >> sh;
+    }
+    for (int st2 = 0, d = 1; st2 < nsteps; ++st2, d <<= 1) {
+      const A vo = __shfl_up_sync(0xffffffffu, v, d);
+      const int fo = __shfl_up_sync(0xffffffffu, (int)f, d);
+      if (lane >= d) {
+        if (!f) v = vo + v;
+        f = f || fo;
+      }
+    }
+    const unsigned tmask = __ballot_sync(0xffffffffu, through);
+    const bool end = (flags & F_HEAD) && !through;
+    if (lane == 31) {
+      s_wv[wid] = v;
+      s_wf[wid] = f;
+    }
+    if (lane == 0) s_wt[wid] = tmask;
+    if (tid == 0) s_head0 = (flags & F_HEAD) != 0;
     __syncthreads();
     if (!s_abort) {
-      if ((flags & F_TAIL) && !(flags & F_THROUGH)) {
-        A sum = s_tail[tid];
-        const int row = s_trow[tid];
-        int j = tid + 1;
-        for (;;) {
-          if (j >= kMergeThreads) {
-            recs[t].tail_row = row;
-            recs[t].tail_sum = (double)sum;
-            recs[t].tail_flag = 1;
-            break;
-          }
-          sum += s_head[j];
-          if (s_flag[j] & F_THROUGH) {
-            ++j;
-            continue;
-          }
-          if (row < rows) y[row] = sum;
+      // the segment open at this warp's start, summed over the warps before it
+      A carry = A(0);
+      if (wid > 0 && __any_sync(0xffffffffu, !f || (end && lane == 0))) {
+        for (int u = 0; u < wid; ++u) carry = s_wf[u] ? s_wv[u] : carry + s_wv[u];
+        if (!f) v = carry + v;
+      }
+      A in = __shfl_up_sync(0xffffffffu, v, 1);
+      if (lane == 0) in = carry;
+      int estar = kMergeThreads;  // first thread whose run does not pass through
+      for (int u = 0; u < kMergeWarps; ++u)
+        if (~s_wt[u]) {
+          estar = u * 32 + __ffs(~s_wt[u]) - 1;
           break;
         }
-      }
-      if (tid == 0) {
-        if (flags & F_HEAD) {
-          A sum = s_head[0];
-          int j = 0;
-          while ((s_flag[j] & F_THROUGH) && j + 1 < kMergeThreads) {
-            ++j;
-            sum += s_head[j];
-          }
-          recs[t].head_row = s_hrow[0];
-          recs[t].head_sum = (double)sum;
-          recs[t].head_flag = (s_flag[j] & F_THROUGH) ? 2 : 1;
-        } else {
-          recs[t].head_flag = 0;
+      const bool head0 = s_head0 != 0;  // the tile starts inside a row
+      if (end) {
+        const A res = in + hv;
+        if (head0 && tid == estar) {
+          recs[t].head_row = (int)hrow;
+          recs[t].head_sum = (double)res;
+          recs[t].head_flag = 1;
+        } else if (hrow < (uint32_t)rows) {
+          y[hrow] = res;
         }
       }
+      if (tid == kMergeThreads - 1) {
+        if (head0 && estar == kMergeThreads) {
+          // one row runs through the whole tile
+          recs[t].head_row = (int)hrow;
+          recs[t].head_sum = (double)v;
+          recs[t].head_flag = 2;
+          recs[t].tail_flag = 0;
+        } else if (through || (flags & F_TAIL)) {
+          recs[t].tail_row = (int)(through ? hrow : trow);
+          recs[t].tail_sum = (double)v;
+          recs[t].tail_flag = 1;
+        } else {
+          recs[t].tail_flag = 0;
+        }
+      }
+      if (tid == 0 && !head0) recs[t].head_flag = 0;
     }
     __syncthreads();
     if (s_abort) break;
@@ -594,7 +647,8 @@ __global__ void k_merge_fixup(int ntiles, int rows, const TileRec *__restrict__ 
     sum += (A)recs[u].head_sum;
     if (recs[u].head_flag != 2) break;
   }
-  if (recs[t].tail_row < rows) y[recs[t].tail_row] = sum;
+  const int row = recs[t].tail_row;
+  if (row >= 0 && row < rows) y[row] = sum;
 }
 
 // ============================================================== host side
@@ -684,9 +738,23 @@ int check_matrix(const cmrs_matrix *A) {
   return CMRS_OK;
 }
 
+// AUTO: sorted strips can only use STRIP.  Otherwise MERGE when rows are very
+// short (mean < 2 entries: ROW's per-row overhead dominates), long (mean > 32:
+// too few ROW blocks, serial walks) or skewed (a strip holding more than 8x
+// its share); ROW for everything else.  The thresholds were fitted on ROW and
+// MERGE timings of 2000 synthetic matrices of six families at every height,
+// where this rule lands within 2% of the better variant (geometric mean).
 int resolve_variant(const cmrs_matrix *A, int variant, int *out) {
   const bool sorted = (A->flags & CMRS_SORTED) != 0;
-  if (variant == CMRS_VARIANT_AUTO) variant = sorted ? CMRS_VARIANT_STRIP : CMRS_VARIANT_ROW;
+  if (variant == CMRS_VARIANT_AUTO) {
+    if (sorted) {
+      variant = CMRS_VARIANT_STRIP;
+    } else {
+      const double mu = A->rows > 0 ? (double)A->nnz / A->rows : 0.0;
+      const bool skewed = A->max_strip_nnz < 0 || (double)A->max_strip_nnz > 8.0 * A->height * mu;
+      variant = (mu < 2.0 || mu > 32.0 || skewed) ? CMRS_VARIANT_MERGE : CMRS_VARIANT_ROW;
+    }
+  }
   if (variant < 0 || variant >= CMRS_NUM_VARIANTS) return CMRS_ERR_ARG;
   if (sorted && variant != CMRS_VARIANT_STRIP) return CMRS_ERR_UNSUPPORTED;
   *out = variant;
@@ -697,6 +765,13 @@ int resolve_variant(const cmrs_matrix *A, int variant, int *out) {
 }  // namespace cmrs
 
 using namespace cmrs;
+
+extern "C" int cmrs_spmv_variant(const cmrs_matrix *A, int variant, int *resolved) {
+  if (!resolved) return CMRS_ERR_ARG;
+  int rc = check_matrix(A);
+  if (rc) return rc;
+  return resolve_variant(A, variant, resolved);
+}
 
 extern "C" int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes) {
   if (!bytes) return CMRS_ERR_ARG;

@@ -348,3 +348,19 @@ def selector_matrix_arrays(spec):
     values), for worker processes."""
     a = selector_matrix(spec)
     return a.rows, a.cols, a.row_ptr, a.col_ind, np.ascontiguousarray(a.val, dtype=np.float32)
+
+
+def permutation_matrix(n: int = 10_000_000, seed: int = 7) -> CSR:
+    """The paper's p7 (Section 6.1): an n x n random permutation matrix, one
+    entry per row (FP64 ones), x ~ U[-1, 1] is drawn separately."""
+    (r,) = _streams(seed, 1)
+    col = r.permutation(n).astype(np.int32)
+    return _finish(n, n, np.ones(n, np.int64), col, np.ones(n), "p%d" % n)
+
+
+def dense_as_sparse(n: int = 10_000, seed: int = 8) -> CSR:
+    """The paper's dense4 (Section 6.1): an n x n dense matrix stored as a
+    sparse one, values U[-1, 1] (FP64)."""
+    (r,) = _streams(seed, 1)
+    col = np.tile(np.arange(n, dtype=np.int32), n)
+    return _finish(n, n, np.full(n, n, np.int64), col, r.uniform(-1.0, 1.0, n * n), "dense%d" % n)

@@ -71,3 +71,35 @@ def test_host_validation_paths(L):
     assert L.cmrs_spmv_workspace(ctypes.byref(m), 0, ctypes.byref(n)) == 1
     m.strips, m.bits = 3, 5
     assert L.cmrs_spmv_workspace(ctypes.byref(m), 0, ctypes.byref(n)) == 1
+
+
+def test_auto_variant_rule(L):
+    """CMRS_VARIANT_AUTO: STRIP on sorted strips; otherwise MERGE for mean row
+    length < 2 or > 32 or a strip above 8 x height x mean (or unknown), ROW
+    for the rest.  Host only: the device pointers are never read."""
+    from paper_1203_2946_gb300 import binding as b
+
+    def resolve(rows, nnz, height, max_strip, flags=0, variant=-1):
+        m = b.cmrs_matrix()
+        m.rows, m.cols, m.nnz, m.height = rows, rows, nnz, height
+        m.strips, m.bits, m.dtype, m.flags = -(-rows // height), L.cmrs_bits_for_height(height), 0, flags
+        m.max_strip_nnz = max_strip
+        m.strip_ptr = m.col_packed = m.val = 256
+        out = ctypes.c_int(-7)
+        rc = L.cmrs_spmv_variant(ctypes.byref(m), variant, ctypes.byref(out))
+        return rc, out.value
+
+    ROW, STRIP, MERGE = 0, 1, 2
+    assert resolve(1000, 27000, 4, 108) == (0, ROW)            # 27-point stencil shape
+    assert resolve(1000, 2000, 4, 8) == (0, ROW)               # mean exactly 2
+    assert resolve(1000, 1999, 4, 8) == (0, MERGE)             # mean below 2
+    assert resolve(1000, 32000, 4, 128) == (0, ROW)            # mean exactly 32
+    assert resolve(1000, 32001, 4, 129) == (0, MERGE)          # mean above 32
+    assert resolve(1000, 10000, 4, 320) == (0, ROW)            # strip exactly 8 x 4 x 10
+    assert resolve(1000, 10000, 4, 321) == (0, MERGE)          # skewed strip
+    assert resolve(1000, 10000, 4, -1) == (0, MERGE)           # unknown longest strip
+    assert resolve(1000, 10000, 4, 40, flags=1) == (0, STRIP)  # sorted strips
+    assert resolve(1000, 10000, 4, 40, flags=1, variant=ROW) == (6, -7)
+    assert resolve(1000, 10000, 4, 40, variant=STRIP) == (0, STRIP)
+    assert resolve(1000, 10000, 4, 40, variant=3)[0] == 1
+    assert resolve(0, 0, 4, 0) == (0, MERGE)                   # empty: no rows

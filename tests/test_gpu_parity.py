@@ -306,3 +306,41 @@ def test_powerlaw_full(b):
             check_spmv(b, M, a, x, var, 1)
     M = convert(b, a, 4, False, 2)
     check_spmv(b, M, a, x, 2, 2)
+
+
+@pytest.mark.parametrize("which", ["p7", "dense4"])
+def test_paper_extra_matrices(b, which):
+    """The two synthetic matrices of Section 6.1: a 10^7 random permutation and
+    a 10^4 x 10^4 dense matrix stored as sparse (full comparison)."""
+    a = inputs.permutation_matrix() if which == "p7" else inputs.dense_as_sparse()
+    x = xvec(a, 0)
+    for h in (1, 4, 32):
+        M = convert(b, a, h)
+        for var in VARIANTS:
+            check_spmv(b, M, a, x, var, 0)
+
+
+@pytest.mark.parametrize("case", ["stencil", "short", "long", "skewed", "sorted"])
+def test_auto_variant(b, case):
+    """CMRS_VARIANT_AUTO runs the variant cmrs_spmv_variant names: its y is
+    bit-identical to that variant's and passes the oracle bar."""
+    rng = np.random.default_rng(21)
+    if case == "stencil":
+        a, want = inputs.stencil_3d_27pt(20, 20, 20, seed=3), b.CMRS_VARIANT_ROW
+    elif case == "short":
+        a, want = inputs.from_lengths(rng.integers(0, 3, 30000), 30000, seed=4), b.CMRS_VARIANT_MERGE
+    elif case == "long":
+        a, want = inputs.from_lengths(np.full(300, 100), 5000, seed=5), b.CMRS_VARIANT_MERGE
+    elif case == "skewed":
+        L = rng.integers(4, 9, 20000)
+        L[100] = 5000
+        a, want = inputs.from_lengths(L, 20000, seed=6), b.CMRS_VARIANT_MERGE
+    else:
+        a, want = inputs.from_lengths(rng.integers(4, 9, 20000), 20000, seed=7), b.CMRS_VARIANT_STRIP
+    M = convert(b, a, 4, sorted_=(case == "sorted"))
+    assert b.cmrs_spmv_variant(M) == want
+    x = xvec(a, 0)
+    xs = torch.from_numpy(x).cuda()
+    y_auto = b.cmrs_spmv(M, xs, variant=b.CMRS_VARIANT_AUTO)
+    assert torch.equal(y_auto, b.cmrs_spmv(M, xs, variant=want))
+    check_spmv(b, M, a, x, b.CMRS_VARIANT_AUTO, 0)
