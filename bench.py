@@ -60,6 +60,19 @@ def beta_plus(nnz, rows, strips, s_v, s_i=4):
     return (s_v + s_i) * nnz + s_i * strips + 2 * s_v * rows
 
 
+def beta_minus(nnz, rows, strips, s_v, s_i=4):
+    """Eq. 6.1, input vector not cached: one x read per nonzero."""
+    return (2 * s_v + s_i) * nnz + s_i * strips + s_v * rows
+
+
+def eta(nnz, rows, strips, s_v, ms, peak):
+    """beta_-/t, and eta_+- = beta_+-/t / B (B = the measured copy bandwidth)."""
+    t = ms / 1e3
+    bm = beta_minus(nnz, rows, strips, s_v) / t / 1e9
+    return {"beta_minus_gbs": bm, "eta_plus": beta_plus(nnz, rows, strips, s_v) / t / 1e9 / peak,
+            "eta_minus": bm / peak}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -335,6 +348,7 @@ def run_ours(args):
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU"},
         "gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
         "gflops_paper": (2 * a.nnz - a.rows) / (per_ms / 1e3) / 1e9,
+        "eta": eta(a.nnz, a.rows, strips, 8, per_ms, peak),
         "pct_of_hbm_peak": 100.0 * (value / world) / peak,
         "pct_of_nominal_8tbs": 100.0 * (value / world) / 8000.0,
         "paper_protocol": {"mean_ms": statistics.mean(trimmed), "std_ms": statistics.pstdev(trimmed),
@@ -527,6 +541,7 @@ def run_secondary(args):
         yref, scale = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val.astype(np.float64), x.astype(np.float64))
         rel = np.abs(yd.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
         extra = {"gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
+                 "eta": eta(a.nnz, a.rows, S, sv, per_ms, peak),
                  "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))}}
         if not args.no_cpu:
             extra["cpu_baseline"] = cpu_oracle_rate(inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind,

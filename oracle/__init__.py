@@ -56,6 +56,8 @@ def lib():
         _lib.orc_mlp_backward.argtypes = [i, i, i, i] + [vp] * 15
         _lib.orc_mlp_backward.restype = d
         _lib.orc_adam_step.argtypes = [i, vp, vp, vp, vp, i, d, d, d, d]
+        _lib.orc_pad_arrange.argtypes = [i, i, i, vp, vp, vp, vp, vp]
+        _lib.orc_pad_arrange.restype = i
     return _lib
 
 
@@ -135,6 +137,25 @@ def cmrs_spmv(rows, height, strip_ptr, packed, val, x):
     y = np.empty(int(rows), np.float64)
     lib().orc_cmrs_spmv(int(rows), int(height), _p(sp), _p(pk), _p(v), _p(xx), _p(y))
     return y
+
+
+def pad_arrange(rows, height, strip_ptr, packed, slots=8):
+    """Section 6.6 modified CMRS: strips rearranged into 32-item chunks with at
+    most `slots` contiguous items per row per chunk, zero-filled.  Returns
+    dict(strip_ptr, packed, src) with src[i] = source position or -1 (zero)."""
+    sp, pk = _c(strip_ptr, np.int32), _c(packed, np.uint32)
+    h = int(height)
+    out_sp = np.empty(sp.size, np.int32)
+    rc = lib().orc_pad_arrange(int(rows), h, int(slots), _p(sp), _p(pk), _p(out_sp), None, None)
+    if rc:
+        raise OracleError(rc)
+    n = int(out_sp[-1])
+    out_pk = np.empty(n, np.uint32)
+    src = np.empty(n, np.int64)
+    rc = lib().orc_pad_arrange(int(rows), h, int(slots), _p(sp), _p(pk), _p(out_sp), _p(out_pk), _p(src))
+    if rc:
+        raise OracleError(rc)
+    return dict(strip_ptr=out_sp, packed=out_pk, src=src)
 
 
 _STORE_DT = {F64: (np.float64, 1), F32: (np.float32, 1), BF16: (np.uint16, 1), BF16X2: (np.uint16, 2)}

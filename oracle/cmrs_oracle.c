@@ -526,3 +526,114 @@ void orc_adam_step(int n, double *p, const double *g, double *m, double *v,
     p[k] = p[k] - lr * mh / (sqrt(vh) + eps);
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Section 6.6, modified CMRS.  Algorithm 1's per-warp buffer shrinks from
+ * 32 x HEIGHT to M x HEIGHT when the lane that takes an item adds into slot
+ * (lane mod M) of the item's row; that is race-free when two items of one
+ * row handled in the same 32-item warp pass sit at positions that differ
+ * mod M.  The section obtains this by rearranging each strip -- at most M
+ * items of a row per pass, stored contiguously -- with explicit zeroes where
+ * needed, and pads every strip to a multiple of 32 items.  The arrangement
+ * itself is left open; the reading used here:
+ *   - a strip becomes a sequence of 32-item chunks (one warp pass each);
+ *   - as few chunks as the strip allows: C = max(ceil(items / 32),
+ *     ceil(longest row / M)) for the items still left;
+ *   - per chunk, every row first takes what it must so that the rest fits in
+ *     C - 1 chunks, max(0, left - M (C - 1)) items (these fit: they sum to
+ *     at most 32); the room still free then goes to rows in order of most
+ *     items left after that (ties: lower row first), each topped up to
+ *     min(M, left) items, until the chunk holds 32 items; items are taken in
+ *     CRS order;
+ *   - room still left is filled with zero items, rows 0 upwards, each row
+ *     topped up to M items in the chunk (height * M >= 32 leaves room);
+ *   - inside a chunk the rows appear in ascending order, each as one run:
+ *     its real items, then its zero items.
+ * A zero item has column 0 and value +0.0.  Input: unsorted strips
+ * (RowInStrip non-decreasing inside each strip).  Output: the new StripPtr
+ * (multiples of 32), the packed words, and src[i] = source position of item
+ * i, or -1 for a zero item.  packed_out and src_out may be NULL (sizes
+ * only).  Returns ORC_BAD_ARG for height * slots < 32 or a count overflow. */
+int orc_pad_arrange(int rows, int height, int slots, const int32_t *strip_ptr,
+                    const uint32_t *packed, int32_t *strip_ptr_out,
+                    uint32_t *packed_out, int64_t *src_out) {
+  int bits = orc_bits_for_height(height);
+  if (bits < 0 || slots < 1 || slots > 32 || height * slots < 32) return ORC_BAD_ARG;
+  int strips = (rows + height - 1) / height;
+  uint32_t mask = (1u << bits) - 1;
+  int64_t out = 0;
+  strip_ptr_out[0] = 0;
+  for (int s = 0; s < strips; ++s) {
+    int64_t next[32], left[32];
+    for (int r = 0; r < 32; ++r) left[r] = 0;
+    for (int32_t k = strip_ptr[s]; k < strip_ptr[s + 1]; ++k) {
+      uint32_t r = packed[k] & mask;
+      if ((int)r >= height) return ORC_BAD_ARG;
+      left[r] += 1;
+    }
+    /* rows are contiguous runs in RowInStrip order inside an unsorted strip */
+    int64_t at = strip_ptr[s];
+    for (int r = 0; r < height; ++r) {
+      next[r] = at;
+      at += left[r];
+    }
+    for (;;) {
+      int64_t total = 0;
+      for (int r = 0; r < height; ++r) total += left[r];
+      if (total == 0) break;
+      int64_t longest = 0;
+      for (int r = 0; r < height; ++r)
+        if (left[r] > longest) longest = left[r];
+      int64_t chunks = (total + 31) / 32;
+      if ((longest + slots - 1) / slots > chunks) chunks = (longest + slots - 1) / slots;
+      int take[32], pad[32], served[32];
+      for (int r = 0; r < 32; ++r) take[r] = pad[r] = served[r] = 0;
+      int room = 32;
+      for (int r = 0; r < height; ++r) {
+        int64_t must = left[r] - (int64_t)slots * (chunks - 1);
+        if (must > 0) {
+          take[r] = (int)must;
+          room -= (int)must;
+        }
+      }
+      if (room < 0) return ORC_BAD_ARG; /* cannot happen: the musts sum to at most 32 */
+      while (room > 0) {
+        int best = -1;
+        for (int r = 0; r < height; ++r)
+          if (!served[r] && left[r] - take[r] > 0 && take[r] < slots &&
+              (best < 0 || left[r] - take[r] > left[best] - take[best]))
+            best = r;
+        if (best < 0) break;
+        served[best] = 1;
+        int64_t cap = left[best] < slots ? left[best] : slots;
+        int64_t t = cap - take[best];
+        if (t > room) t = room;
+        take[best] += (int)t;
+        room -= (int)t;
+      }
+      for (int r = 0; r < height && room > 0; ++r) {
+        int e = slots - take[r];
+        if (e > room) e = room;
+        pad[r] = e;
+        room -= e;
+      }
+      for (int r = 0; r < height; ++r) {
+        for (int j = 0; j < take[r]; ++j) {
+          if (packed_out) packed_out[out] = packed[next[r]];
+          if (src_out) src_out[out] = next[r];
+          next[r] += 1;
+          out += 1;
+        }
+        left[r] -= take[r];
+        for (int j = 0; j < pad[r]; ++j) {
+          if (packed_out) packed_out[out] = (uint32_t)r;
+          if (src_out) src_out[out] = -1;
+          out += 1;
+        }
+      }
+    }
+    if (out > 2147483647) return ORC_BAD_ARG;
+    strip_ptr_out[s + 1] = (int32_t)out;
+  }
+  return ORC_OK;
+}
