@@ -44,9 +44,13 @@ def args_parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--height", type=int, default=None, help="strip height (default: 4; power-law and p7 32)")
-    p.add_argument("--variant", default=None, choices=["row", "strip", "merge", "auto"],
-                   help="SpMV kernel variant (default: row; power-law merge; p7 and dense4 auto)")
+    p.add_argument("--height", type=int, default=None,
+                   help="strip height (default: 32 for the 27-point headline, power-law and p7; else 4)")
+    p.add_argument("--slots", type=int, default=1, help="padded variant: slots per row per warp pass (M of "
+                   "Section 6.6; 1, 2, 4 or 8)")
+    p.add_argument("--variant", default=None, choices=["row", "strip", "merge", "auto", "padded"],
+                   help="SpMV kernel variant (default: padded for the 27-point headline; power-law merge; "
+                        "p7 and dense4 auto; else row)")
     p.add_argument("--workload", default="stencil27",
                    choices=["stencil27", "powerlaw", "batched", "laplacian", "p7", "dense4"],
                    help="stencil27 is the headline; the others print the same JSON schema for their workload")
@@ -281,7 +285,8 @@ def run_ours(args):
     from paper_1203_2946_gb300 import binding as b, inputs
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    variant = binding_variant = b.VARIANTS[args.variant]
+    variant = binding_variant = dict(b.VARIANTS, auto=b.CMRS_VARIANT_AUTO,
+                                     padded=b.CMRS_VARIANT_PADDED)[args.variant]
     a, x = inputs.workload_stencil27_128()
     h = args.height
     strips = (a.rows + h - 1) // h
@@ -289,6 +294,10 @@ def run_ours(args):
     ci = torch.from_numpy(a.col_ind).to(dev)
     va = torch.from_numpy(a.val).to(dev)
     M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F64)
+    M_csr = M
+    if args.variant == "padded":
+        M = b.cmrs_pad(M, args.slots)  # Section 6.6 arrangement; bytes_per_step stays the unpadded beta+
+    variant = b.cmrs_spmv_variant(M, binding_variant)
     xd = torch.from_numpy(x).to(dev)
     yd = torch.empty(a.rows, dtype=torch.float64, device=dev)
     ws = M.spmv_workspace(variant)
@@ -335,15 +344,18 @@ def run_ours(args):
     e2e_times = time_steps(e2e_step, e2e_steps, flush, stream)
     e2e_ms = max_over_ranks(dist, statistics.mean(e2e_times))
 
-    kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge"}[variant]
+    kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[variant]
     trimmed = sorted(times)[:-1] if len(times) > 1 else times
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "27-point stencil 128^3 (n=2097152, nnz=55742968), FP64 values and x, "
-                               "CMRS h=%d, variant %s" % (h, args.variant),
+                               + ("modified CMRS (Section 6.6) h=%d, M=%d slot(s) per row per pass" % (h, args.slots)
+                                  if args.variant == "padded" else "CMRS h=%d, variant %s" % (h, args.variant)),
                    "height": h, "variant": args.variant, "bytes_per_step": bp,
+                   "slots": args.slots if args.variant == "padded" else None,
+                   "stored_items_per_nnz": M.nnz / a.nnz,
                    "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events",
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU"},
         "gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
@@ -355,7 +367,8 @@ def run_ours(args):
                            "min_ms": min(times)},
         "roofline": {"bound": "hbm", "achieved": bp / (per_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": bp / (per_ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind + " (hbm_gbs)",
-                     "traffic": traffic_record(kname, "stencil27_128_f64_h%d" % h), "kernel": kname},
+                     "traffic": traffic_record(kname, "stencil27_128_f64_h%d" % h + (
+                         "_m%d" % args.slots if args.variant == "padded" else "")), "kernel": kname},
         "e2e": {"value": world * bp / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(a.rows * 8),
                 "ms_per_step": e2e_ms, "note": "x host->device, cmrs_spmv, y device->host; matrix resident"},
@@ -364,10 +377,13 @@ def run_ours(args):
         "wall_s_timed_region": wall,
     }
     if rank == 0 and not args.no_extras and world == 1:
-        line["forms"] = storage_forms(b, a, x, rp, ci, va, h, flush, stream, per_ms)
-        line["variants_f64"] = variant_sweep(b, a, xd, M, flush, stream, bp)
+        line["forms"] = storage_forms(b, a, x, rp, ci, va, h, flush, stream, per_ms,
+                                      args.slots if args.variant == "padded" else None)
+        line["variants_f64"] = variant_sweep(b, a, xd, M_csr, flush, stream, bp)
+        line["modified_cmrs"] = modified_cmrs(b, a, xd, rp, ci, va, flush, stream)
         line["heights_f64_row"] = height_sweep(b, a, xd, rp, ci, va, flush, stream)
-        line["conversion"] = conversion_times(b, a, rp, ci, va, M, h)
+        line["conversion"] = conversion_times(b, a, rp, ci, va, M_csr, h,
+                                              args.slots if args.variant == "padded" else None)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(a, x, strips)
     if rank == 0:
@@ -376,10 +392,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def storage_forms(b, a, x, rp, ci, va, h, flush, stream, f64_ms, steps=200):
-    """FP32 / BF16 / split-BF16 storage of the same matrix: speed, speed-up over
-    the FP64 kernel and error against the FP64 oracle (max and median of
-    |y - y*| / (|A||x|)_i)."""
+def storage_forms(b, a, x, rp, ci, va, h, flush, stream, f64_ms, slots=None, steps=200):
+    """FP32 / BF16 / split-BF16 storage of the same matrix, in the headline's
+    format (padded with `slots` per row per pass, else plain CMRS with ROW):
+    speed, speed-up over the FP64 kernel and error against the FP64 oracle
+    (max and median of |y - y*| / (|A||x|)_i)."""
     import oracle
     import torch
     yref, scale = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val, x)
@@ -388,11 +405,14 @@ def storage_forms(b, a, x, rp, ci, va, h, flush, stream, f64_ms, steps=200):
     strips = (a.rows + h - 1) // h
     for name, dt, sv in (("f32", b.CMRS_F32, 4), ("bf16", b.CMRS_BF16, 2), ("bf16x2", b.CMRS_BF16X2, 4)):
         M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=dt)
+        v = b.CMRS_VARIANT_ROW
+        if slots:
+            M, v = b.cmrs_pad(M, slots), b.CMRS_VARIANT_PADDED
         y = torch.empty(a.rows, dtype=torch.float32, device=va.device)
-        ws = M.spmv_workspace(0)
+        ws = M.spmv_workspace(v)
         for _ in range(3):
-            b.cmrs_spmv(M, x32, y, 0, ws)
-        ts = time_steps(lambda: b.cmrs_spmv(M, x32, y, 0, ws), steps, flush, stream)
+            b.cmrs_spmv(M, x32, y, v, ws)
+        ts = time_steps(lambda: b.cmrs_spmv(M, x32, y, v, ws), steps, flush, stream)
         ms = statistics.mean(ts)
         rel = np.abs(y.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
         bp = beta_plus(a.nnz, a.rows, strips, sv if name != "bf16x2" else 4) if name != "bf16" else \
@@ -406,7 +426,7 @@ def storage_forms(b, a, x, rp, ci, va, h, flush, stream, f64_ms, steps=200):
     return out
 
 
-def conversion_times(b, a, rp, ci, va, M, h, reps=5):
+def conversion_times(b, a, rp, ci, va, M, h, slots=None, reps=5):
     """CRS -> CMRS (plain and strip-sorted) and CMRS -> CRS on the same matrix:
     median wall time of `reps` calls (each call synchronises once), and GB/s
     over the arrays read and written (24 B per entry + the pointer arrays)."""
@@ -429,6 +449,10 @@ def conversion_times(b, a, rp, ci, va, M, h, reps=5):
         out[name] = {"ms": ms, "gbs": moved / (ms / 1e3) / 1e9}
     ms = tm(lambda: b.cmrs_to_csr(M))
     out["to_csr_f64"] = {"ms": ms, "gbs": moved / (ms / 1e3) / 1e9}
+    if slots:
+        # Section 6.6 arrangement of the plain CMRS matrix (layout pass, one read-back, fill pass)
+        ms = tm(lambda: b.cmrs_pad(M, slots))
+        out["to_padded_f64_m%d" % slots] = {"ms": ms, "gbs": moved / (ms / 1e3) / 1e9}
     out["note"] = "includes the binding's output allocations and one status read-back per call"
     return out
 
@@ -449,6 +473,26 @@ def height_sweep(b, a, xd, rp, ci, va, flush, stream, steps=60):
     return out
 
 
+def modified_cmrs(b, a, xd, rp, ci, va, flush, stream, steps=100):
+    """Section 6.6: padded strips and the slot-buffer kernel, FP64, at the
+    paper's height 16 and M = 8 and at other (height, M); GB/s on the unpadded
+    beta+."""
+    import torch
+    out = {}
+    y = torch.empty(a.rows, dtype=torch.float64, device=xd.device)
+    for h, m in ((16, 8), (32, 8), (16, 2), (32, 2), (32, 1)):
+        P = b.cmrs_pad(b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F64), m)
+        ws = P.spmv_workspace(b.CMRS_VARIANT_PADDED)
+        for _ in range(3):
+            b.cmrs_spmv(P, xd, y, b.CMRS_VARIANT_PADDED, ws)
+        ms = statistics.mean(time_steps(lambda: b.cmrs_spmv(P, xd, y, b.CMRS_VARIANT_PADDED, ws), steps, flush,
+                                        stream))
+        bp = beta_plus(a.nnz, a.rows, (a.rows + h - 1) // h, 8)
+        out["h%d_m%d" % (h, m)] = {"ms": ms, "gbs": bp / (ms / 1e3) / 1e9, "padded_items_per_nnz": P.nnz / a.nnz}
+        del P
+    return out
+
+
 def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
     import torch
     out = {}
@@ -464,10 +508,11 @@ def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
 
 def main():
     args = args_parse()
-    if args.height is None:
-        args.height = 32 if args.workload in ("powerlaw", "p7") else 4
     if args.variant is None:
-        args.variant = {"powerlaw": "merge", "p7": "auto", "dense4": "auto"}.get(args.workload, "row")
+        args.variant = {"stencil27": "padded", "powerlaw": "merge", "p7": "auto", "dense4": "auto"}.get(
+            args.workload, "row")
+    if args.height is None:
+        args.height = 32 if args.workload in ("powerlaw", "p7") or args.variant == "padded" else 4
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stencil27":
@@ -520,10 +565,12 @@ def run_secondary(args):
             a, x = inputs.workload_laplacian_64()
             dt, sv, name = b.CMRS_F64, 8, "f64"
             wl = "5-point Laplacian 64x64 (n=4096, nnz=20224), FP64"
-        h, v = args.height, dict(b.VARIANTS, auto=b.CMRS_VARIANT_AUTO)[args.variant]
+        h, v = args.height, dict(b.VARIANTS, auto=b.CMRS_VARIANT_AUTO, padded=b.CMRS_VARIANT_PADDED)[args.variant]
         rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
         va = torch.from_numpy(np.ascontiguousarray(a.val)).to(dev)
         M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=dt)
+        if args.variant == "padded":
+            M = b.cmrs_pad(M, args.slots)
         ran = b.cmrs_spmv_variant(M, v)
         xd = torch.from_numpy(x).to(dev)
         yd = torch.empty(a.rows, dtype=xd.dtype, device=dev)
@@ -549,6 +596,10 @@ def run_secondary(args):
         if args.workload in ("p7", "dense4"):
             var = {}
             for vn, vv in b.VARIANTS.items():
+                try:
+                    b.cmrs_spmv_variant(M, vv)
+                except b.CmrsError:
+                    continue  # not defined on this matrix (padded strips)
                 vws = M.spmv_workspace(vv)
                 g = lambda: b.cmrs_spmv(M, xd, yd, vv, vws)  # noqa: E731
                 for _ in range(2):
@@ -589,10 +640,10 @@ def run_secondary(args):
         for _ in range(3):
             e2e()
         e_ms = statistics.mean(time_steps(e2e, max(20, min(steps, 200)), flush, stream))
-        kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge"}[ran]
+        kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[ran]
         line = _line(args, gbs, "GB/s", per_ms, name,
                      {"workload": wl, "height": h, "variant": args.variant,
-                      "kernel_variant": ("row", "strip", "merge")[ran], "bytes_per_step": bp,
+                      "kernel_variant": ("row", "strip", "merge", "padded")[ran], "bytes_per_step": bp,
                       "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
                      {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                       "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": kname},

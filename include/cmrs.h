@@ -62,6 +62,16 @@ extern "C" {
 /* Section 4, fourth optimisation: entries of each strip ordered by column
  * (stable: equal columns keep their CRS order). */
 #define CMRS_SORTED 1u
+/* Section 6.6 ("modified CMRS"): strips rearranged into 32-item warp passes
+ * holding at most M items of any one row, stored contiguously, filled with
+ * explicit zero items (column 0, value +0); every strip holds a multiple of
+ * 32 items.  M (slots) is 1, 2, 4 or 8, kept as log2(M) in flag bits 8..10;
+ * the paper's M is 8.  Made by cmrs_pad_layout + cmrs_pad_fill. */
+#define CMRS_PADDED 2u
+#define CMRS_PAD_SLOTS 8 /* the paper's M */
+#define CMRS_PAD_SLOTS_SHIFT 8
+#define CMRS_PAD_SLOTS_MASK (7u << CMRS_PAD_SLOTS_SHIFT)
+#define CMRS_PAD_SLOTS_OF(flags) (1 << (((flags) & CMRS_PAD_SLOTS_MASK) >> CMRS_PAD_SLOTS_SHIFT))
 
 /* ---- SpMV kernel variants -------------------------------------------------
  * Every variant computes the same y = A x; they differ in how threads are
@@ -79,7 +89,15 @@ extern "C" {
  *                       of consecutive entries, rows that cross thread or
  *                       tile boundaries are joined afterwards in a fixed
  *                       order.  Needs unsorted strips.  Best for skewed rows.
- *   CMRS_VARIANT_AUTO   (-1) STRIP for sorted strips.  Otherwise, with
+ *   CMRS_VARIANT_PADDED the Section 6.6 kernel, only for CMRS_PADDED
+ *                       matrices: one warp per strip, lane l adds each
+ *                       product into slot (l mod M) of its row in a per-warp
+ *                       shared buffer, the slots of each row are summed at
+ *                       the strip's end (M = 1: lane r keeps row r's sum in a
+ *                       register, no buffer).  Fully coalesced 32-bit loads,
+ *                       no search for row starts.
+ *   CMRS_VARIANT_AUTO   (-1) PADDED for padded strips, STRIP for sorted
+ *                       strips.  Otherwise, with
  *                       mu = nnz / rows: MERGE if mu < 2, mu > 32, or
  *                       max_strip_nnz > 8 * height * mu (or unknown, -1);
  *                       ROW for the rest.  cmrs_spmv_variant reports the
@@ -88,7 +106,8 @@ extern "C" {
 #define CMRS_VARIANT_ROW 0
 #define CMRS_VARIANT_STRIP 1
 #define CMRS_VARIANT_MERGE 2
-#define CMRS_NUM_VARIANTS 3
+#define CMRS_VARIANT_PADDED 3
+#define CMRS_NUM_VARIANTS 4
 
 /* A CMRS matrix: a view of caller-owned device arrays (Section 3).
  *   strips     = ceil(rows / height)
@@ -158,6 +177,39 @@ int cmrs_to_csr_workspace(const cmrs_matrix *A, size_t *bytes);
 int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *col_ind_out, void *val_out,
                 void *workspace, size_t workspace_bytes, void *stream);
 
+/* ---- modified CMRS (Section 6.6) ------------------------------------------
+ * Rearranges an unsorted CMRS matrix A (not itself padded) into the padded
+ * form with M = slots in {1, 2, 4, 8} (height * slots >= 32, else
+ * CMRS_ERR_HEIGHT; bad slots: CMRS_ERR_ARG).  Each strip becomes
+ * C = max(ceil(items / 32), ceil(longest row / M)) passes of 32 items -- the
+ * fewest possible.  Per pass, every row first takes the items it must for
+ * the rest to fit in the passes left, then free room goes to rows with the
+ * most items left (ties: lower row); rows appear in ascending order, each as
+ * one run of at most M items (its next items in A's order, then its zero
+ * items); free room after that is zero items, rows 0 upwards, each topped up
+ * to M.  With M = 1 (so height 32) every pass holds one item of each row,
+ * row r at position r: the SpMV kernel then keeps each row's sum in a
+ * register.  A smaller M shortens the kernel's final slot sums but pads rows
+ * longer than M * (items / 32) -- fit for regular rows, not skewed ones.
+ * Same storage form as A (BF16X2: hi then lo at 2 * cmrs_pad8(nnz_padded)
+ * bytes).
+ *
+ * cmrs_pad_layout: writes the padded StripPtr (device, [strips+1], multiples
+ * of 32) and the padded item count (host *nnz_padded).  Synchronises
+ * `stream` once to read the count.  CMRS_ERR_ARG if the count reaches 2^31,
+ * CMRS_ERR_UNSUPPORTED for sorted or padded input, CMRS_ERR_HEIGHT for
+ * height < 4.  workspace: >= cmrs_pad_workspace() bytes, 256-byte aligned.
+ * cmrs_pad_fill: writes col_packed_out[nnz_padded] and val_out (device,
+ * cmrs_val_bytes(nnz_padded, A->dtype) bytes, 16-byte aligned) and *out (a
+ * view of strip_ptr_padded, col_packed_out and val_out with CMRS_PADDED set).
+ * Asynchronous.  A padded matrix multiplies x[0] by zero in its zero items:
+ * x must be finite there.  cmrs_to_csr does not accept padded matrices. */
+int cmrs_pad_workspace(const cmrs_matrix *A, int slots, size_t *bytes);
+int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_ptr_padded, int32_t *nnz_padded,
+                    void *workspace, size_t workspace_bytes, void *stream);
+int cmrs_pad_fill(const cmrs_matrix *A, int slots, const int32_t *strip_ptr_padded, int32_t nnz_padded,
+                  uint32_t *col_packed_out, void *val_out, void *stream, cmrs_matrix *out);
+
 /* ---- SpMV, y = A x (Section 4, Algorithm 1) ------------------------------
  * x: device [cols], y: device [rows], double for CMRS_F64 else float.  y is
  * overwritten (rows without entries get 0).  A's arrays are trusted (as built
@@ -189,7 +241,7 @@ int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant,
  * file-scope __device__ array, resident on every GPU that loads the library
  * until the process exits).  Limit: A->nnz <= 111,820,800 (58,240 tiles of
  * 1,920 entries); larger matrices return CMRS_ERR_WORKSPACE before any device
- * work.  Unsorted strips only (CMRS_ERR_UNSUPPORTED otherwise).  No
+ * work.  Unsorted, unpadded strips only (CMRS_ERR_UNSUPPORTED otherwise).  No
  * cudaMalloc, cudaFree or other allocating call is made.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress, with
  * that device current), so make that first call before any stream capture.

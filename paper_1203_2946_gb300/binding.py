@@ -17,8 +17,11 @@ LIB_PATH = os.path.join(HERE, "libcmrs.so")
 
 CMRS_OK = 0
 CMRS_F64, CMRS_F32, CMRS_BF16, CMRS_BF16X2 = 0, 1, 2, 3
-CMRS_SORTED = 1
+CMRS_SORTED, CMRS_PADDED = 1, 2
+CMRS_PAD_SLOTS = 8  # the paper's M
+CMRS_PAD_SLOTS_SHIFT = 8
 CMRS_VARIANT_AUTO, CMRS_VARIANT_ROW, CMRS_VARIANT_STRIP, CMRS_VARIANT_MERGE = -1, 0, 1, 2
+CMRS_VARIANT_PADDED = 3
 VARIANTS = {"row": 0, "strip": 1, "merge": 2}
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2, "bf16x2": 3}
 _STORED = {0: torch.float64, 1: torch.float32, 2: torch.int16, 3: torch.int16}
@@ -74,6 +77,9 @@ def lib():
             "cmrs_to_csr": ([M, vp, vp, vp, vp, sz, vp], i),
             "cmrs_spmv_workspace": ([M, i, ctypes.POINTER(sz)], i),
             "cmrs_spmv_variant": ([M, i, ctypes.POINTER(ctypes.c_int)], i),
+            "cmrs_pad_workspace": ([M, i, ctypes.POINTER(sz)], i),
+            "cmrs_pad_layout": ([M, i, vp, ctypes.POINTER(ctypes.c_int32), vp, sz, vp], i),
+            "cmrs_pad_fill": ([M, i, vp, ctypes.c_int32, vp, vp, vp, M], i),
             "cmrs_spmv": ([M, vp, vp, i, vp, sz, vp], i),
             "cmrs_spmv_check": ([M, i, vp, vp], i),
             "cmrs_spmv_noalloc": ([M, vp, vp, vp], i),
@@ -198,6 +204,28 @@ def cmrs_from_csr(row_ptr, col_ind, val, cols, height, flags=0, dtype=CMRS_F64, 
     rc = lib().cmrs_from_csr(rows, cols, nnz, _ptr(row_ptr), _ptr(col_ind), _ptr(val), in_dt, height, flags, dtype,
                              _ptr(sp), _ptr(pk), _ptr(vout), _ptr(ws), n.value, _stream(stream), ctypes.byref(m))
     _check(rc, "cmrs_from_csr")
+    return Matrix(m, sp, pk, vout)
+
+
+def cmrs_pad(A: Matrix, slots=CMRS_PAD_SLOTS, stream=None):
+    """Section 6.6 modified CMRS of an unsorted matrix with M = slots (1, 2, 4
+    or 8): a new Matrix with CMRS_PADDED set (cmrs_pad_layout, then
+    cmrs_pad_fill)."""
+    dev = A.col_packed.device
+    n = ctypes.c_size_t()
+    _check(lib().cmrs_pad_workspace(A.ref(), slots, ctypes.byref(n)), "cmrs_pad_workspace")
+    ws = workspace(n.value, dev)
+    sp = torch.empty(A.struct.strips + 1, dtype=torch.int32, device=dev)
+    nnz_p = ctypes.c_int32()
+    _check(lib().cmrs_pad_layout(A.ref(), slots, _ptr(sp), ctypes.byref(nnz_p), _ptr(ws), n.value,
+                                 _stream(stream)), "cmrs_pad_layout")
+    npad = nnz_p.value
+    pk = torch.empty(max(npad, 1), dtype=torch.int32, device=dev)
+    vb = lib().cmrs_val_bytes(npad, A.dtype)
+    vout = torch.empty(max(vb, 16), dtype=torch.uint8, device=dev)
+    m = cmrs_matrix()
+    _check(lib().cmrs_pad_fill(A.ref(), slots, _ptr(sp), npad, _ptr(pk), _ptr(vout), _stream(stream),
+                               ctypes.byref(m)), "cmrs_pad_fill")
     return Matrix(m, sp, pk, vout)
 
 

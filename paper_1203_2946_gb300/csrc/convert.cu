@@ -492,6 +492,7 @@ extern "C" int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *
   if (A->strips != ceil_div(A->rows, A->height)) return CMRS_ERR_ARG;
   if (A->nnz > 0 && (!A->col_packed || !col_ind_out || !A->strip_ptr)) return CMRS_ERR_ARG;
   if (A->dtype < CMRS_F64 || A->dtype > CMRS_BF16X2) return CMRS_ERR_ARG;
+  if (A->flags & CMRS_PADDED) return CMRS_ERR_UNSUPPORTED;  // zero items are not told apart from entries
   uint32_t *status = (workspace && workspace_bytes >= 256) ? reinterpret_cast<uint32_t *>(workspace) : nullptr;
   cudaStream_t st = as_stream(stream);
   const int sms = sm_count();

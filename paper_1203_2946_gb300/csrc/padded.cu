@@ -1,0 +1,359 @@
+// Modified CMRS (Section 6.6): strips rearranged into 32-item warp passes that
+// hold at most M contiguous items of any one row (M = slots, 1..8; the
+// paper's is 8), filled with zero items, so that the SpMV kernel can add
+// each product into slot (lane mod M) of its row's buffer without two lanes
+// of a pass meeting in one slot.  With M = 1 and height 32 every pass holds
+// exactly one item (or zero item) of each row, row r at lane r.
+//
+// One warp per strip, lane r owning row r.  Each pass is planned from the
+// items each row has left: C = max(ceil(total / 32), ceil(longest / M))
+// passes remain; every row first takes max(0, left - M (C - 1)) items (what
+// the remaining C - 1 passes cannot hold), free room then goes to the rows
+// with most items left (ties: lower row) up to min(left, M) each, and room
+// still free becomes zero items, rows 0 upwards, each row topped up to M.
+// Inside a pass the rows appear in ascending order, each one run.  The
+// layout pass runs the plan only to count passes; a scan turns the counts
+// into the padded StripPtr; the fill pass runs the plan again and writes.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace cmrs {
+namespace {
+
+constexpr int kPadWarps = 8;
+constexpr int kScanThreads = 1024;
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t ST_PAD_OVERFLOW = 1u, ST_PAD_PLAN = 2u;
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane) {
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  return incl - v;
+}
+
+// Plans (and with kFill writes) strip s.  Returns its pass count, or -1 if a
+// plan overflowed a pass (cannot happen for valid unsorted strips; kept as a
+// guard so that a corrupt input never writes past its strip).
+template <bool kFill, typename S, bool kSplit>
+__device__ long long pad_strip(int s, int height, int bits, int slots, const int32_t *__restrict__ sp,
+                               const uint32_t *__restrict__ packed, const S *__restrict__ vh,
+                               const S *__restrict__ vl, long long out0, uint32_t *__restrict__ pk_out,
+                               S *__restrict__ vo_h, S *__restrict__ vo_l) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << bits) - 1;
+  const int sa = sp[s], sb = sp[s + 1];
+  // first item of row `lane` (RowInStrip is non-decreasing in an unsorted strip)
+  int start = sa;
+  if (lane > 0 && lane < height) {
+    int lo = sa, hi = sb;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((packed[mid] & mask) < (uint32_t)lane) lo = mid + 1;
+      else hi = mid;
+    }
+    start = lo;
+  }
+  int end = __shfl_down_sync(kFull, start, 1);
+  if (lane == height - 1) end = sb;
+  int left = lane < height ? end - start : 0;
+  int next = start;
+  long long passes = 0;
+  for (;;) {
+    const int total = (int)__reduce_add_sync(kFull, (unsigned)left);
+    if (total == 0) break;
+    const int longest = (int)__reduce_max_sync(kFull, (unsigned)left);
+    const int C = max((total + 31) / 32, (longest + slots - 1) / slots);
+    int take = max(0, left - slots * (C - 1));
+    int room = 32 - (int)__reduce_add_sync(kFull, (unsigned)take);
+    if (room < 0) return -1;
+    // free room: rows with most items left first, lower row on ties
+    const int want = min(left, slots) - take;
+    const unsigned long long key =
+        want > 0 ? ((unsigned long long)(left - take) << 6) | (unsigned long long)(63 - lane) : 0ull;
+    int before = 0;
+    for (int j = 0; j < 32; ++j) {
+      const unsigned long long kj = __shfl_sync(kFull, key, j);
+      const int wj = __shfl_sync(kFull, want, j);
+      if (kj > key) before += wj;
+    }
+    const int extra = want > 0 ? max(0, min(want, room - before)) : 0;
+    take += extra;
+    room -= (int)__reduce_add_sync(kFull, (unsigned)extra);
+    // zero items: rows 0 upwards, each topped up to `slots`
+    const int zcap = lane < height ? slots - take : 0;
+    const int zero = max(0, min(zcap, room - warp_excl_scan(zcap, lane)));
+    const int len = take + zero;
+    const int off = warp_excl_scan(len, lane);
+    if (kFill) {
+      const long long base = out0 + passes * 32 + off;
+      for (int j = 0; j < take; ++j) {
+        pk_out[base + j] = packed[next + j];
+        vo_h[base + j] = vh[next + j];
+        if (kSplit) vo_l[base + j] = vl[next + j];
+      }
+      for (int j = take; j < len; ++j) {
+        pk_out[base + j] = (uint32_t)lane;  // column 0, this row
+        vo_h[base + j] = S(0);
+        if (kSplit) vo_l[base + j] = S(0);
+      }
+    }
+    next += take;
+    left -= take;
+    ++passes;
+  }
+  return passes;
+}
+
+__global__ void __launch_bounds__(kPadWarps * 32) k_pad_count(int strips, int height, int bits, int slots,
+                                                             const int32_t *__restrict__ sp,
+                                                             const uint32_t *__restrict__ packed,
+                                                             int32_t *__restrict__ counts, uint32_t *status) {
+  const int nw = gridDim.x * kPadWarps;
+  for (int s = blockIdx.x * kPadWarps + (threadIdx.x >> 5); s < strips; s += nw) {
+    const long long c = pad_strip<false, uint32_t, false>(s, height, bits, slots, sp, packed, nullptr, nullptr, 0,
+                                                          nullptr, nullptr, nullptr);
+    if ((threadIdx.x & 31) == 0) {
+      if (c < 0) atomicOr(status, ST_PAD_PLAN);
+      counts[s] = c < 0 ? 0 : (c > 0x7fffffffLL ? 0x7fffffff : (int32_t)c);
+    }
+  }
+}
+
+template <typename S, bool kSplit>
+__global__ void __launch_bounds__(kPadWarps * 32) k_pad_fill(int strips, int height, int bits, int slots,
+                                                            const int32_t *__restrict__ sp,
+                                                            const uint32_t *__restrict__ packed,
+                                                            const S *__restrict__ vh, const S *__restrict__ vl,
+                                                            const int32_t *__restrict__ sp_out,
+                                                            uint32_t *__restrict__ pk_out, S *__restrict__ vo_h,
+                                                            S *__restrict__ vo_l) {
+  const int nw = gridDim.x * kPadWarps;
+  for (int s = blockIdx.x * kPadWarps + (threadIdx.x >> 5); s < strips; s += nw)
+    pad_strip<true, S, kSplit>(s, height, bits, slots, sp, packed, vh, vl, sp_out[s], pk_out, vo_h, vo_l);
+}
+
+// ---- inclusive scan of the pass counts into the padded StripPtr
+// Block-local inclusive scan (int64) of counts, block totals into aux.
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(int n, const int32_t *__restrict__ in,
+                                                               long long *__restrict__ incl,
+                                                               long long *__restrict__ aux) {
+  __shared__ long long wsum[kScanThreads / 32];
+  const int i = blockIdx.x * kScanThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long v = i < n ? in[i] : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) wsum[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    long long t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long u = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += u;
+    }
+    wsum[lane] = t;
+  }
+  __syncthreads();
+  if (w > 0) v += wsum[w - 1];
+  if (i < n) incl[i] = v;
+  if (threadIdx.x == kScanThreads - 1) aux[blockIdx.x] = v;
+}
+
+// Exclusive scan of the block totals, in place, by one block.
+__global__ void __launch_bounds__(kScanThreads) k_scan_aux(int nb, long long *__restrict__ aux) {
+  __shared__ long long wsum[kScanThreads / 32];
+  __shared__ long long carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int i = b0 + threadIdx.x;
+    const long long x = i < nb ? aux[i] : 0;
+    long long v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(kFull, v, o);
+      if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      long long t = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(kFull, t, o);
+        if (lane >= o) t += u;
+      }
+      wsum[lane] = t;
+    }
+    __syncthreads();
+    if (w > 0) v += wsum[w - 1];
+    const long long c = carry;
+    if (i < nb) aux[i] = c + v - x;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = c + v;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_finish(int n, const long long *__restrict__ incl, const long long *__restrict__ aux,
+                              int32_t *__restrict__ sp_out, uint32_t *status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) sp_out[0] = 0;
+  if (i >= n) return;
+  const long long items = 32 * (incl[i] + aux[i / kScanThreads]);
+  if (items > 0x7fffffffLL) {
+    atomicOr(status, ST_PAD_OVERFLOW);
+    sp_out[i + 1] = 0x7fffffff;
+  } else {
+    sp_out[i + 1] = (int32_t)items;
+  }
+}
+
+struct PadLayout {
+  size_t counts, incl, aux, total;
+};
+
+PadLayout pad_layout_ws(int strips) {
+  PadLayout L;
+  const size_t nb = (size_t)ceil_div(strips > 0 ? strips : 1, kScanThreads);
+  L.counts = 256;
+  L.incl = L.counts + align256((size_t)(strips > 0 ? strips : 1) * 4);
+  L.aux = L.incl + align256((size_t)(strips > 0 ? strips : 1) * 8);
+  L.total = L.aux + align256(nb * 8);
+  return L;
+}
+
+int slots_log2(int slots) {
+  for (int k = 0; k <= 3; ++k)
+    if (slots == (1 << k)) return k;
+  return -1;
+}
+
+int check_pad_input(const cmrs_matrix *A, int slots) {
+  if (slots_log2(slots) < 0) return CMRS_ERR_ARG;
+  if (!A) return CMRS_ERR_ARG;
+  if (A->rows < 0 || A->cols < 0 || A->nnz < 0) return CMRS_ERR_ARG;
+  const int bits = cmrs_bits_for_height(A->height);
+  if (bits < 0) return CMRS_ERR_HEIGHT;
+  if (A->bits != bits || A->strips != ceil_div(A->rows, A->height)) return CMRS_ERR_ARG;
+  if (A->dtype < CMRS_F64 || A->dtype > CMRS_BF16X2) return CMRS_ERR_ARG;
+  if (A->flags & ~(CMRS_SORTED | CMRS_PADDED | CMRS_PAD_SLOTS_MASK)) return CMRS_ERR_ARG;
+  if (A->flags) return CMRS_ERR_UNSUPPORTED;  // sorted strips, or already padded
+  if (A->height * slots < 32) return CMRS_ERR_HEIGHT;
+  if (A->rows > 0 && !A->strip_ptr) return CMRS_ERR_ARG;
+  if (A->nnz > 0 && (!A->col_packed || !A->val)) return CMRS_ERR_ARG;
+  return CMRS_OK;
+}
+
+int pad_grid(int strips) {
+  static int sms = 0;
+  if (sms == 0) sms = sm_count();
+  return (int)std::min<long long>(ceil_div(strips, kPadWarps), (long long)sms * 8);
+}
+
+template <typename S, bool kSplit>
+int launch_fill(const cmrs_matrix *A, int slots, const int32_t *sp_out, int nnz_padded, uint32_t *pk_out,
+                void *val_out, cudaStream_t st) {
+  const S *vh = reinterpret_cast<const S *>(A->val);
+  const S *vl = kSplit ? vh + cmrs_pad8(A->nnz) : nullptr;
+  S *oh = reinterpret_cast<S *>(val_out);
+  S *ol = kSplit ? oh + cmrs_pad8(nnz_padded) : nullptr;
+  k_pad_fill<S, kSplit><<<pad_grid(A->strips), kPadWarps * 32, 0, st>>>(A->strips, A->height, A->bits, slots,
+                                                                        A->strip_ptr, A->col_packed, vh, vl, sp_out,
+                                                                        pk_out, oh, ol);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
+}  // namespace
+}  // namespace cmrs
+
+using namespace cmrs;
+
+extern "C" int cmrs_pad_workspace(const cmrs_matrix *A, int slots, size_t *bytes) {
+  if (!bytes) return CMRS_ERR_ARG;
+  const int rc = check_pad_input(A, slots);
+  if (rc) return rc;
+  *bytes = pad_layout_ws(A->strips).total;
+  return CMRS_OK;
+}
+
+extern "C" int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_ptr_padded, int32_t *nnz_padded,
+                               void *workspace, size_t workspace_bytes, void *stream) {
+  int rc = check_pad_input(A, slots);
+  if (rc) return rc;
+  if (!strip_ptr_padded || !nnz_padded) return CMRS_ERR_ARG;
+  const PadLayout L = pad_layout_ws(A->strips);
+  if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return CMRS_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  char *ws = reinterpret_cast<char *>(workspace);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+  int32_t *counts = reinterpret_cast<int32_t *>(ws + L.counts);
+  long long *incl = reinterpret_cast<long long *>(ws + L.incl);
+  long long *aux = reinterpret_cast<long long *>(ws + L.aux);
+  CMRS_CUDA_TRY(cudaMemsetAsync(status, 0, 4, st));
+  const int S = A->strips;
+  if (S == 0) {
+    CMRS_CUDA_TRY(cudaMemsetAsync(strip_ptr_padded, 0, 4, st));
+    *nnz_padded = 0;
+    CMRS_CUDA_TRY(cudaStreamSynchronize(st));
+    return CMRS_OK;
+  }
+  k_pad_count<<<pad_grid(S), kPadWarps * 32, 0, st>>>(S, A->height, A->bits, slots, A->strip_ptr, A->col_packed,
+                                                      counts, status);
+  CMRS_LAUNCH_CHECK();
+  const int nb = (int)ceil_div(S, kScanThreads);
+  k_scan_blocks<<<nb, kScanThreads, 0, st>>>(S, counts, incl, aux);
+  CMRS_LAUNCH_CHECK();
+  k_scan_aux<<<1, kScanThreads, 0, st>>>(nb, aux);
+  CMRS_LAUNCH_CHECK();
+  k_scan_finish<<<(int)ceil_div(S, 256), 256, 0, st>>>(S, incl, aux, strip_ptr_padded, status);
+  CMRS_LAUNCH_CHECK();
+  uint32_t host[2] = {0, 0};
+  CMRS_CUDA_TRY(cudaMemcpyAsync(&host[0], status, 4, cudaMemcpyDeviceToHost, st));
+  CMRS_CUDA_TRY(cudaMemcpyAsync(&host[1], strip_ptr_padded + S, 4, cudaMemcpyDeviceToHost, st));
+  CMRS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (host[0] & ST_PAD_PLAN) return CMRS_ERR_CSR_INVALID;
+  if (host[0] & ST_PAD_OVERFLOW) return CMRS_ERR_ARG;
+  *nnz_padded = (int32_t)host[1];
+  return CMRS_OK;
+}
+
+extern "C" int cmrs_pad_fill(const cmrs_matrix *A, int slots, const int32_t *strip_ptr_padded, int32_t nnz_padded,
+                             uint32_t *col_packed_out, void *val_out, void *stream, cmrs_matrix *out) {
+  int rc = check_pad_input(A, slots);
+  if (rc) return rc;
+  if (!out || nnz_padded < 0 || (nnz_padded & 31)) return CMRS_ERR_ARG;
+  if (A->rows > 0 && !strip_ptr_padded) return CMRS_ERR_ARG;
+  if (nnz_padded > 0 && (!col_packed_out || !val_out)) return CMRS_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(col_packed_out) | reinterpret_cast<uintptr_t>(val_out)) & 15) return CMRS_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  if (A->strips > 0 && nnz_padded > 0) {
+    switch (A->dtype) {
+      case CMRS_F64: rc = launch_fill<double, false>(A, slots, strip_ptr_padded, nnz_padded, col_packed_out, val_out, st); break;
+      case CMRS_F32: rc = launch_fill<float, false>(A, slots, strip_ptr_padded, nnz_padded, col_packed_out, val_out, st); break;
+      case CMRS_BF16: rc = launch_fill<uint16_t, false>(A, slots, strip_ptr_padded, nnz_padded, col_packed_out, val_out, st); break;
+      default: rc = launch_fill<uint16_t, true>(A, slots, strip_ptr_padded, nnz_padded, col_packed_out, val_out, st); break;
+    }
+    if (rc) return rc;
+  }
+  *out = *A;
+  out->nnz = nnz_padded;
+  out->flags = CMRS_PADDED | ((uint32_t)slots_log2(slots) << CMRS_PAD_SLOTS_SHIFT);
+  out->max_strip_nnz = -1;
+  out->strip_ptr = strip_ptr_padded;
+  out->col_packed = col_packed_out;
+  out->val = val_out;
+  return CMRS_OK;
+}

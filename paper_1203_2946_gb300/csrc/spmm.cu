@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_one(Desc d, int rows_per_
 int check_item(const cmrs_matrix *A, int k, const float *X, float *Y) {
   if (!A || k < 1) return CMRS_ERR_ARG;
   if (A->dtype != CMRS_F32) return CMRS_ERR_UNSUPPORTED;
-  if (A->flags & CMRS_SORTED) return CMRS_ERR_UNSUPPORTED;
+  if (A->flags & (CMRS_SORTED | CMRS_PADDED)) return CMRS_ERR_UNSUPPORTED;
   if (cmrs_bits_for_height(A->height) != A->bits) return CMRS_ERR_HEIGHT;
   if (A->rows < 0 || A->nnz < 0 || A->strips != ceil_div(A->rows, A->height)) return CMRS_ERR_ARG;
   if (A->rows > 0 && (!A->strip_ptr || !Y)) return CMRS_ERR_ARG;

@@ -373,6 +373,110 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_spmv_strip(int rows, int h
   }
 }
 
+// ============================================================== PADDED mapping
+// Section 6.6: one warp per strip of a padded matrix.  Every 32-item pass of
+// the strip holds each row as one run of at most M items (M = slots), so
+// lane l adds its product into slot (l mod M) of its row in a per-warp
+// buffer buf[row][slot] without meeting another lane of the pass (a row's run
+// covers consecutive words: at most 2-way bank conflicts, where a
+// [slot][row] layout put a whole run in one bank); passes follow each other
+// behind a warp barrier (the next pass may touch a slot another lane wrote).
+// At the strip's end each row's M slots are summed by G = min(M, 32 / h2)
+// lanes (h2 = height rounded up to a power of 2), M / G slots each, then a
+// butterfly over the G lanes.  M = 1 (height 32): row r sits at lane r in
+// every pass, so lane r keeps row r's sum in a register -- no buffer, no
+// barrier, no final sum.  Loads are plain coalesced 32-bit ones, kPadU
+// passes in flight per warp.
+#ifndef CMRS_PAD_U
+#define CMRS_PAD_U 4
+#endif
+constexpr int kPadWarps = 8;
+constexpr int kPadU = CMRS_PAD_U;  // passes whose loads are in flight together
+
+template <int DT>
+__device__ __forceinline__ typename Form<DT>::Acc ld_val_stream(const typename Form<DT>::Stored *hi,
+                                                                const typename Form<DT>::Stored *lo, long long k,
+                                                                uint64_t pol) {
+  if constexpr (DT == CMRS_F64 || DT == CMRS_F32) {
+    return ld_stream(hi + k, pol);
+  } else if constexpr (DT == CMRS_BF16) {
+    return bf16_bits_to_float(ld_stream(hi + k, pol));
+  } else {
+    return bf16_bits_to_float(ld_stream(hi + k, pol)) + bf16_bits_to_float(ld_stream(lo + k, pol));
+  }
+}
+
+template <int DT, int kM>
+__global__ void __launch_bounds__(kPadWarps * 32) k_spmv_padded(int rows, int height, int bits, int strips,
+                                                               const int32_t *__restrict__ sp,
+                                                               const uint32_t *__restrict__ packed,
+                                                               const typename Form<DT>::Stored *__restrict__ hi,
+                                                               const typename Form<DT>::Stored *__restrict__ lo,
+                                                               const typename Form<DT>::Acc *__restrict__ x,
+                                                               typename Form<DT>::Acc *__restrict__ y) {
+  typedef typename Form<DT>::Acc A;
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  A *buf = reinterpret_cast<A *>(smem) + (size_t)w * kM * height;
+  const uint32_t mask = (1u << bits) - 1;
+  const int slot = lane & (kM - 1);
+  const uint64_t pol = policy_evict_first();
+  const int nw = gridDim.x * kPadWarps;
+  int h2 = 1;
+  while (h2 < height) h2 <<= 1;
+  const int G = kM < 32 / h2 ? kM : 32 / h2;  // lanes summing one row's slots
+  const int per = kM / G;
+  for (int s = blockIdx.x * kPadWarps + w; s < strips; s += nw) {
+    A acc = A(0);
+    if (kM > 1) {
+      for (int i = lane; i < kM * height; i += 32) buf[i] = A(0);
+      __syncwarp();
+    }
+    const int a = sp[s], b = sp[s + 1];  // multiples of 32
+    for (int k0 = a; k0 < b; k0 += 32 * kPadU) {
+      uint32_t c[kPadU];
+      A v[kPadU], xv[kPadU];
+#pragma unroll
+      for (int u = 0; u < kPadU; ++u)
+        if (k0 + 32 * u < b) {  // warp-uniform
+          const long long k = (long long)k0 + 32 * u + lane;
+          c[u] = ld_stream(packed + k, pol);
+          v[u] = ld_val_stream<DT>(hi, lo, k, pol);
+        }
+#pragma unroll
+      for (int u = 0; u < kPadU; ++u)
+        if (k0 + 32 * u < b) xv[u] = ld_x(x + (c[u] >> bits));
+#pragma unroll
+      for (int u = 0; u < kPadU; ++u)
+        if (k0 + 32 * u < b) {
+          if (kM == 1) {
+            acc = fma_acc(v[u], xv[u], acc);
+          } else {
+            A *p = buf + (c[u] & mask) * kM + slot;
+            *p = fma_acc(v[u], xv[u], *p);
+            __syncwarp();
+          }
+        }
+    }
+    const long long row0 = (long long)s * height;
+    if (kM == 1) {
+      if (row0 + lane < rows) y[row0 + lane] = acc;
+    } else {
+      __syncwarp();
+      const int r = lane / G, part = lane - r * G;
+      A sum = A(0);
+      if (r < height) {
+        const A *q = buf + r * kM + part * per;
+        sum = q[0];
+        for (int m = 1; m < per; ++m) sum += q[m];
+      }
+      for (int o = G >> 1; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (part == 0 && r < height && row0 + r < rows) y[row0 + r] = sum;
+      __syncwarp();
+    }
+  }
+}
+
 // ============================================================== MERGE mapping
 // Tile t = entries [1920 t, 1920 t + 1920), staged by bulk copies; thread i
 // owns the 15 consecutive entries from 1920 t + 15 i.  It finds their strip by
@@ -678,6 +782,21 @@ size_t merge_ws_bytes(int nnz) {
   return 256 + align256((size_t)(ntiles + 1) * 4) + align256((size_t)ntiles * sizeof(TileRec));
 }
 
+template <int DT, int kM>
+int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, const typename Form<DT>::Stored *lo,
+                  const typename Form<DT>::Acc *x, typename Form<DT>::Acc *y, cudaStream_t st) {
+  typedef typename Form<DT>::Acc Acc;
+  static Occ occ;
+  const size_t smem = (size_t)kPadWarps * kM * A->height * sizeof(Acc);
+  const int per_sm = occupancy(k_spmv_padded<DT, kM>, kPadWarps * 32, (size_t)kPadWarps * kM * 32 * sizeof(Acc), occ);
+  const long long need = ceil_div(A->strips, kPadWarps);
+  const int grid = (int)std::min<long long>(need, (long long)per_sm * sm_count());
+  k_spmv_padded<DT, kM><<<grid, kPadWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->strip_ptr,
+                                                             A->col_packed, hi, lo, x, y);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
 template <int DT>
 int launch(const cmrs_matrix *A, const void *xv, void *yv, int variant, char *ws, cudaStream_t st) {
   typedef typename Form<DT>::Stored S;
@@ -706,6 +825,13 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, int variant, char *ws
     k_spmv_strip<DT><<<grid, kStripWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->strip_ptr,
                                                            A->col_packed, hi, lo, x, y);
     CMRS_LAUNCH_CHECK();
+  } else if (variant == CMRS_VARIANT_PADDED) {
+    switch (CMRS_PAD_SLOTS_OF(A->flags)) {
+      case 1: return launch_padded<DT, 1>(A, hi, lo, x, y, st);
+      case 2: return launch_padded<DT, 2>(A, hi, lo, x, y, st);
+      case 4: return launch_padded<DT, 4>(A, hi, lo, x, y, st);
+      default: return launch_padded<DT, 8>(A, hi, lo, x, y, st);
+    }
   } else {
     static Occ occ;
     const int ntiles = (int)ceil_div(A->nnz, kMergeTile);
@@ -732,7 +858,13 @@ int check_matrix(const cmrs_matrix *A) {
   if (A->bits != cmrs_bits_for_height(A->height)) return CMRS_ERR_ARG;
   if (A->strips != ceil_div(A->rows, A->height)) return CMRS_ERR_ARG;
   if (A->dtype < CMRS_F64 || A->dtype > CMRS_BF16X2) return CMRS_ERR_ARG;
-  if (A->flags & ~CMRS_SORTED) return CMRS_ERR_ARG;
+  if (A->flags & ~(CMRS_SORTED | CMRS_PADDED | CMRS_PAD_SLOTS_MASK)) return CMRS_ERR_ARG;
+  if ((A->flags & CMRS_SORTED) && (A->flags & CMRS_PADDED)) return CMRS_ERR_ARG;
+  if (!(A->flags & CMRS_PADDED) && (A->flags & CMRS_PAD_SLOTS_MASK)) return CMRS_ERR_ARG;
+  if (A->flags & CMRS_PADDED) {
+    const int m = CMRS_PAD_SLOTS_OF(A->flags);
+    if (m > 8 || A->height * m < 32 || (A->nnz & 31)) return CMRS_ERR_ARG;
+  }
   if (A->rows > 0 && !A->strip_ptr) return CMRS_ERR_ARG;
   if (A->nnz > 0 && (!A->col_packed || !A->val)) return CMRS_ERR_ARG;
   return CMRS_OK;
@@ -746,8 +878,11 @@ int check_matrix(const cmrs_matrix *A) {
 // where this rule lands within 2% of the better variant (geometric mean).
 int resolve_variant(const cmrs_matrix *A, int variant, int *out) {
   const bool sorted = (A->flags & CMRS_SORTED) != 0;
+  const bool padded = (A->flags & CMRS_PADDED) != 0;
   if (variant == CMRS_VARIANT_AUTO) {
-    if (sorted) {
+    if (padded) {
+      variant = CMRS_VARIANT_PADDED;
+    } else if (sorted) {
       variant = CMRS_VARIANT_STRIP;
     } else {
       const double mu = A->rows > 0 ? (double)A->nnz / A->rows : 0.0;
@@ -757,6 +892,9 @@ int resolve_variant(const cmrs_matrix *A, int variant, int *out) {
   }
   if (variant < 0 || variant >= CMRS_NUM_VARIANTS) return CMRS_ERR_ARG;
   if (sorted && variant != CMRS_VARIANT_STRIP) return CMRS_ERR_UNSUPPORTED;
+  // padded strips: Algorithm 1 or the Section 6.6 kernel; that kernel needs padded strips
+  if (padded && variant != CMRS_VARIANT_STRIP && variant != CMRS_VARIANT_PADDED) return CMRS_ERR_UNSUPPORTED;
+  if (!padded && variant == CMRS_VARIANT_PADDED) return CMRS_ERR_UNSUPPORTED;
   *out = variant;
   return CMRS_OK;
 }
@@ -796,7 +934,7 @@ extern "C" int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int varia
   const size_t need = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz) : 256;
   if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CMRS_ERR_WORKSPACE;
   // ROW and MERGE stream col_packed and val with bulk copies: 16-byte aligned bases
-  if (v != CMRS_VARIANT_STRIP && A->nnz > 0 &&
+  if ((v == CMRS_VARIANT_ROW || v == CMRS_VARIANT_MERGE) && A->nnz > 0 &&
       ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(A->val)) & 15))
     return CMRS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
@@ -863,7 +1001,7 @@ int noalloc_scratch(void **out) {
 extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, void *stream) {
   int rc = check_matrix(A);
   if (rc) return rc;
-  if (A->flags & CMRS_SORTED) return CMRS_ERR_UNSUPPORTED;
+  if (A->flags & (CMRS_SORTED | CMRS_PADDED)) return CMRS_ERR_UNSUPPORTED;
   if (A->rows == 0) return CMRS_OK;
   if (!y || (A->nnz > 0 && !x)) return CMRS_ERR_ARG;
   if (merge_ws_bytes(A->nnz) > kNoAllocBytes) return CMRS_ERR_WORKSPACE;

@@ -101,5 +101,39 @@ def test_auto_variant_rule(L):
     assert resolve(1000, 10000, 4, 40, flags=1) == (0, STRIP)  # sorted strips
     assert resolve(1000, 10000, 4, 40, flags=1, variant=ROW) == (6, -7)
     assert resolve(1000, 10000, 4, 40, variant=STRIP) == (0, STRIP)
-    assert resolve(1000, 10000, 4, 40, variant=3)[0] == 1
+    assert resolve(1000, 10000, 4, 40, variant=3) == (6, -7)   # PADDED needs padded strips
+    assert resolve(1000, 10000, 4, 40, variant=4)[0] == 1
+    PADDED, P8, P1 = 3, 2 | (3 << 8), 2 | (0 << 8)                    # padded, M = 8 / M = 1
+    assert resolve(1000, 10016, 16, -1, flags=P8) == (0, PADDED)       # padded strips (Section 6.6)
+    assert resolve(1000, 10016, 32, -1, flags=P1) == (0, PADDED)
+    assert resolve(1000, 10016, 16, -1, flags=P8, variant=STRIP) == (0, STRIP)
+    assert resolve(1000, 10016, 16, -1, flags=P8, variant=ROW) == (6, -7)
+    assert resolve(1000, 10016, 16, -1, flags=P8, variant=MERGE) == (6, -7)
+    assert resolve(1000, 10016, 16, -1, flags=P8 | 1)[0] == 1          # sorted and padded
+    assert resolve(1000, 10000, 16, -1, flags=P8)[0] == 1              # padded count not a multiple of 32
+    assert resolve(1000, 10016, 2, -1, flags=P8)[0] == 1               # 2 rows x 8 slots < 32 lanes
+    assert resolve(1000, 10016, 16, -1, flags=P1)[0] == 1              # 16 rows x 1 slot < 32 lanes
+    assert resolve(1000, 10016, 16, -1, flags=2 | (4 << 8))[0] == 1    # 16 slots: not a padded form
+    assert resolve(1000, 10000, 16, -1, flags=3 << 8)[0] == 1          # slot bits without the padded flag
     assert resolve(0, 0, 4, 0) == (0, MERGE)                   # empty: no rows
+
+
+def test_pad_host_validation(L):
+    """cmrs_pad_workspace: host-only checks of the Section 6.6 conversion input."""
+    from paper_1203_2946_gb300 import binding as b
+    m = b.cmrs_matrix()
+    m.rows, m.cols, m.nnz, m.height, m.strips, m.bits, m.dtype = 100, 100, 500, 16, 7, 4, 0
+    m.strip_ptr = m.col_packed = m.val = 256
+    n = ctypes.c_size_t()
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 8, ctypes.byref(n)) == 0 and n.value >= 256
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 2, ctypes.byref(n)) == 0
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 1, ctypes.byref(n)) == 2   # 16 rows x 1 slot < 32 lanes
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 3, ctypes.byref(n)) == 1   # slots not a power of 2
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 16, ctypes.byref(n)) == 1  # slots above 8
+    m.flags = 1
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 8, ctypes.byref(n)) == 6   # sorted strips
+    m.flags = 2 | (3 << 8)
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 8, ctypes.byref(n)) == 6   # already padded
+    m.flags, m.height, m.strips = 0, 2, 50
+    assert L.cmrs_pad_workspace(ctypes.byref(m), 8, ctypes.byref(n)) == 2   # 2 x 8 slots < 32 lanes
+    assert L.cmrs_pad_workspace(None, 8, ctypes.byref(n)) == 1

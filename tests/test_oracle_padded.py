@@ -57,20 +57,32 @@ def check_arrangement(rows, h, cm, pad, slots=M):
         assert (b1 - a1) // 32 == max(-(-T // 32), -(-Lmax // slots))
 
 
-def arrange(a, h):
+def arrange(a, h, slots=M):
     cm = oracle.csr_to_cmrs(a.row_ptr, a.col_ind, a.val, a.cols, h)
-    return cm, oracle.pad_arrange(a.rows, h, cm["strip_ptr"], cm["packed"], M)
+    return cm, oracle.pad_arrange(a.rows, h, cm["strip_ptr"], cm["packed"], slots)
 
 
-@pytest.mark.parametrize("h", [4, 5, 8, 16, 17, 32])
-def test_random_strips(h):
-    rng = np.random.default_rng(h)
+@pytest.mark.parametrize("h,slots", [(4, 8), (5, 8), (8, 8), (16, 8), (17, 8), (32, 8), (8, 4), (16, 2),
+                                     (17, 2), (32, 1)])
+def test_random_strips(h, slots):
+    rng = np.random.default_rng(h * 10 + slots)
     for trial in range(6):
         L = rng.integers(0, [3, 12, 40, 120][trial % 4], 300)
         L[rng.integers(0, 300, 3)] = rng.integers(0, 200, 3)  # a few long rows
         a = inputs.from_lengths(L, 500, seed=trial)
-        cm, pad = arrange(a, h)
-        check_arrangement(a.rows, h, cm, pad)
+        cm, pad = arrange(a, h, slots)
+        check_arrangement(a.rows, h, cm, pad, slots)
+
+
+def test_one_slot_is_row_per_lane():
+    """M = 1 at height 32: every pass holds one item of each row, row r at
+    position r -- the layout in which the kernel keeps row sums in registers."""
+    L = np.random.default_rng(9).integers(0, 40, 320)
+    a = inputs.from_lengths(L, 500, seed=9)
+    cm, pad = arrange(a, 32, 1)
+    check_arrangement(a.rows, 32, cm, pad, 1)
+    ris = pad["packed"] & 31
+    assert np.array_equal(ris.reshape(-1, 32), np.tile(np.arange(32, dtype=np.uint32), (ris.size // 32, 1)))
 
 
 def test_spmv_unchanged():
