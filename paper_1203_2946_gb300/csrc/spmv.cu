@@ -390,6 +390,9 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_spmv_strip(int rows, int h
 #ifndef CMRS_PAD_U
 #define CMRS_PAD_U 4
 #endif
+#ifndef CMRS_PAD_MINB
+#define CMRS_PAD_MINB 6  // resident CTAs per SM asked of the register allocator (7 and 8 spill)
+#endif
 constexpr int kPadWarps = 8;
 constexpr int kPadU = CMRS_PAD_U;  // passes whose loads are in flight together
 
@@ -407,7 +410,7 @@ __device__ __forceinline__ typename Form<DT>::Acc ld_val_stream(const typename F
 }
 
 template <int DT, int kM>
-__global__ void __launch_bounds__(kPadWarps * 32) k_spmv_padded(int rows, int height, int bits, int strips,
+__global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(int rows, int height, int bits, int strips,
                                                                const int32_t *__restrict__ sp,
                                                                const uint32_t *__restrict__ packed,
                                                                const typename Form<DT>::Stored *__restrict__ hi,
