@@ -58,6 +58,9 @@ def lib():
         _lib.orc_adam_step.argtypes = [i, vp, vp, vp, vp, i, d, d, d, d]
         _lib.orc_pad_arrange.argtypes = [i, i, i, vp, vp, vp, vp, vp]
         _lib.orc_pad_arrange.restype = i
+        _lib.orc_row_order.argtypes = [i, vp, i, vp]
+        _lib.orc_row_order.restype = i
+        _lib.orc_permute_csr.argtypes = [i, vp, vp, vp, vp, vp, vp, vp]
     return _lib
 
 
@@ -156,6 +159,28 @@ def pad_arrange(rows, height, strip_ptr, packed, slots=8):
     if rc:
         raise OracleError(rc)
     return dict(strip_ptr=out_sp, packed=out_pk, src=src)
+
+
+def row_order(row_ptr, window):
+    """Row reordering: windows of `window` rows, each by length (longest
+    first, ties in original order).  perm[i] = original row at position i."""
+    rp = _c(row_ptr, np.int32)
+    perm = np.empty(rp.size - 1, np.int32)
+    rc = lib().orc_row_order(rp.size - 1, _p(rp), int(window), _p(perm))
+    if rc:
+        raise OracleError(rc)
+    return perm
+
+
+def permute_csr(row_ptr, col_ind, val, perm):
+    """CRS of P A: row i is the original row perm[i]."""
+    rp, ci, v, pm = _c(row_ptr, np.int32), _c(col_ind, np.int32), _c(val, np.float64), _c(perm, np.int32)
+    rows = rp.size - 1
+    rpo = np.empty(rows + 1, np.int32)
+    cio = np.empty(ci.size, np.int32)
+    vo = np.empty(ci.size, np.float64)
+    lib().orc_permute_csr(rows, _p(rp), _p(ci), _p(v), _p(pm), _p(rpo), _p(cio), _p(vo))
+    return rpo, cio, vo
 
 
 _STORE_DT = {F64: (np.float64, 1), F32: (np.float32, 1), BF16: (np.uint16, 1), BF16X2: (np.uint16, 2)}
