@@ -46,15 +46,16 @@ def args_parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--height", type=int, default=None,
                    help="strip height (default: 32 for the 27-point headline, power-law and p7; else 4)")
-    p.add_argument("--slots", type=int, default=1, help="padded variant: slots per row per warp pass (M of "
-                   "Section 6.6; 1, 2, 4 or 8)")
+    p.add_argument("--slots", type=int, default=None, help="padded variant: slots per row per warp pass (M of "
+                   "Section 6.6; 1, 2, 4 or 8; default 1, irregular 2)")
     p.add_argument("--variant", default=None, choices=["row", "strip", "merge", "auto", "padded"],
                    help="SpMV kernel variant (default: padded for the 27-point headline; power-law merge; "
                         "p7 and dense4 auto; else row)")
     p.add_argument("--workload", default="stencil27",
-                   choices=["stencil27", "powerlaw", "batched", "laplacian", "p7", "dense4"],
+                   choices=["stencil27", "powerlaw", "batched", "laplacian", "p7", "dense4", "irregular"],
                    help="stencil27 is the headline; the others print the same JSON schema for their workload")
     p.add_argument("--batch-count", type=int, default=256, help="batched workload: matrices (256 = full size)")
+    p.add_argument("--window", type=int, default=0, help="irregular workload: row-reordering window (0: none)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary storage-form measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
@@ -513,10 +514,14 @@ def main():
             args.workload, "row")
     if args.height is None:
         args.height = 32 if args.workload in ("powerlaw", "p7") or args.variant == "padded" else 4
+    if args.slots is None:
+        args.slots = 2 if args.workload == "irregular" else 1
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stencil27":
         run_ours(args)
+    elif args.workload == "irregular":
+        run_irregular(args)
     else:
         run_secondary(args)
 
@@ -750,6 +755,116 @@ def _gen_batched(spec):
     from paper_1203_2946_gb300 import inputs
     a, X = inputs.batched_banded(spec)
     return a.row_ptr, a.col_ind, a.val, X
+
+
+
+
+# --------------------------------------------------------------------------- row reordering
+def run_irregular(args):
+    """Banded-random rows of 4..60 entries (n = 2^21, FP64): modified CMRS at
+    h = 32, M = 1 after row reordering (windows of --window rows), the product
+    written back in the original order through the row map; against the same
+    form without reordering, M = 8, and plain CMRS with ROW and MERGE."""
+    import torch
+    from paper_1203_2946_gb300 import build
+    build.build()
+    from paper_1203_2946_gb300 import binding as b, inputs
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peaks()
+    sampler = ClockSampler(None)
+    a, x = inputs.workload_irregular()
+    h, steps = 32, args.steps
+    rp, ci, va = (torch.from_numpy(t).to(dev) for t in (a.row_ptr, a.col_ind, a.val))
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.empty(a.rows, dtype=torch.float64, device=dev)
+    S = (a.rows + h - 1) // h
+    bp = beta_plus(a.nnz, a.rows, S, 8)
+
+    def reorder(window):
+        perm = b.cmrs_row_order(rp, window)
+        rp2, ci2, va2 = b.cmrs_permute_csr(rp, ci, va, perm)
+        return perm, b.cmrs_from_csr(rp2, ci2, va2, a.cols, h, dtype=b.CMRS_F64)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if args.window:
+        perm, M = reorder(args.window)
+    else:
+        perm, M = None, b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F64)
+    P = b.cmrs_pad(M, args.slots)
+    torch.cuda.synchronize()
+    prep_ms = (time.perf_counter() - t0) * 1e3
+    ws = P.spmv_workspace(b.CMRS_VARIANT_PADDED)
+    if perm is None:
+        fn = lambda: b.cmrs_spmv(P, xd, yd, b.CMRS_VARIANT_PADDED, ws)  # noqa: E731
+    else:
+        fn = lambda: b.cmrs_spmv_rows(P, xd, perm, yd, b.CMRS_VARIANT_PADDED, ws)  # noqa: E731
+    for _ in range(max(3, args.warmup)):
+        fn()
+    torch.cuda.synchronize()
+    with sampler:
+        times = time_steps(fn, steps, flush, stream)
+    per_ms = statistics.mean(times)
+    gbs = bp / (per_ms / 1e3) / 1e9
+    yref, scale = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val, x)
+    rel = np.abs(yd.cpu().numpy() - yref) / np.where(scale > 0, scale, 1)
+
+    def timed(f, n=100):
+        for _ in range(3):
+            f()
+        return statistics.mean(time_steps(f, n, flush, stream))
+
+    others = {}
+    M0 = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F64)
+    p256, M256 = reorder(256)
+    p4096, M4096 = reorder(4096)
+    for name, mat, v, rows_map in (
+            ("padded_m1", b.cmrs_pad(M0, 1), b.CMRS_VARIANT_PADDED, None),
+            ("padded_m8", b.cmrs_pad(M0, 8), b.CMRS_VARIANT_PADDED, None),
+            ("reordered_w256_padded_m1", b.cmrs_pad(M256, 1), b.CMRS_VARIANT_PADDED, p256),
+            ("reordered_w4096_padded_m1", b.cmrs_pad(M4096, 1), b.CMRS_VARIANT_PADDED, p4096),
+            ("reordered_w4096_padded_m2", b.cmrs_pad(M4096, 2), b.CMRS_VARIANT_PADDED, p4096),
+            ("row_h32", M0, b.CMRS_VARIANT_ROW, None),
+            ("merge_h32", M0, b.CMRS_VARIANT_MERGE, None),
+            ("reordered_w4096_row_h32", M4096, b.CMRS_VARIANT_ROW, p4096)):
+        w2 = mat.spmv_workspace(v)
+        if rows_map is None:
+            f = lambda mat=mat, v=v, w2=w2: b.cmrs_spmv(mat, xd, yd, v, w2)  # noqa: E731
+        else:
+            f = lambda mat=mat, v=v, w2=w2, pm=rows_map: b.cmrs_spmv_rows(mat, xd, pm, yd, v, w2)  # noqa: E731
+        ms = timed(f)
+        others[name] = {"ms": ms, "gbs": bp / (ms / 1e3) / 1e9, "stored_items_per_nnz": mat.nnz / a.nnz}
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty(a.rows, dtype=torch.float64).pin_memory()
+
+    def e2e():
+        xd.copy_(xh, non_blocking=True)
+        fn()
+        yh.copy_(yd, non_blocking=True)
+    for _ in range(3):
+        e2e()
+    e_ms = statistics.mean(time_steps(e2e, max(20, min(steps, 200)), flush, stream))
+    extra = {"gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9, "eta": eta(a.nnz, a.rows, S, 8, per_ms, peak),
+             "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))},
+             "reorder_pad_prep_ms": prep_ms, "others": others}
+    if not args.no_cpu:
+        extra["cpu_baseline"] = cpu_oracle_rate(a, x, S)
+    line = _line(args, gbs, "GB/s", per_ms, "f64",
+                 {"workload": "banded random n=%d, window 2048, rows of 4..60 entries (nnz=%d), FP64; %smodified "
+                              "CMRS h=32, M=%d" % (a.rows, a.nnz, "rows reordered by length in windows of %d, y through "
+                                                   "the row map; " % args.window if args.window else "", args.slots),
+                  "height": h, "variant": "padded", "slots": args.slots, "window": args.window,
+                  "stored_items_per_nnz": P.nnz / a.nnz, "bytes_per_step": bp,
+                  "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
+                 {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                  "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmv_padded"},
+                 {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(x.nbytes),
+                  "d2h_bytes_per_step": int(a.rows * 8), "ms_per_step": e_ms},
+                 steps, sampler.summary(), extra)
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

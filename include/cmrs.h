@@ -210,6 +210,33 @@ int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_ptr_padded, 
 int cmrs_pad_fill(const cmrs_matrix *A, int slots, const int32_t *strip_ptr_padded, int32_t nnz_padded,
                   uint32_t *col_packed_out, void *val_out, void *stream, cmrs_matrix *out);
 
+/* ---- row reordering (Section 7 outlook; Section 6.3: a low eta_+ is the cue)
+ * An off-line optimisation of CRS input: rows of similar length placed in the
+ * same strip, so that the modified form of Section 6.6 needs fewer zero
+ * items.  The product of the reordered matrix P A is returned in the original
+ * order by cmrs_spmv_rows with row_map = perm.
+ *
+ * cmrs_row_order: perm_out[i] (device int32 [rows]) = the original row placed
+ * at position i.  Inside each window of `window` consecutive rows (1..4096;
+ * the last window may be shorter), rows by length, longest first, equal
+ * lengths in their original order; rows never leave their window, so a
+ * window that is a multiple of the strip height keeps strips local.  row_ptr:
+ * device CRS row pointer.  Asynchronous; no workspace.  CMRS_ERR_ARG for a
+ * window outside 1..4096.
+ *
+ * cmrs_permute_csr: CRS of P A (row i = original row perm[i], entries in their
+ * original order) into row_ptr_out [rows+1], col_ind_out [nnz] and val_out
+ * (val may be NULL: columns only; val_dtype CMRS_F64 or CMRS_F32).  Checks on
+ * the device that perm names every row exactly once and that the row pointer
+ * stays inside [0, nnz] (CMRS_ERR_ARG), and that RowPtr[rows] = nnz
+ * (CMRS_ERR_CSR_INVALID), before writing any column: synchronises `stream`
+ * once.  workspace: >= cmrs_permute_csr_workspace() bytes, 256-byte aligned. */
+int cmrs_row_order(int rows, const int32_t *row_ptr, int window, int32_t *perm_out, void *stream);
+int cmrs_permute_csr_workspace(int rows, size_t *bytes);
+int cmrs_permute_csr(int rows, int nnz, const int32_t *row_ptr, const int32_t *col_ind, const void *val,
+                     int val_dtype, const int32_t *perm, int32_t *row_ptr_out, int32_t *col_ind_out,
+                     void *val_out, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---- SpMV, y = A x (Section 4, Algorithm 1) ------------------------------
  * x: device [cols], y: device [rows], double for CMRS_F64 else float.  y is
  * overwritten (rows without entries get 0).  A's arrays are trusted (as built
@@ -230,6 +257,17 @@ int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes);
 int cmrs_spmv_variant(const cmrs_matrix *A, int variant, int *resolved);
 int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant,
               void *workspace, size_t workspace_bytes, void *stream);
+
+/* y[row_map[i]] = (A x)_i: the product of a row-reordered matrix (A = P B,
+ * row_map = the perm of cmrs_row_order) written in the original row order.
+ * row_map: device int32 [rows], a permutation of 0..rows-1 (entries outside
+ * that range are skipped; a map that is not a permutation leaves some of y
+ * unwritten).  Same arguments, workspace and errors as cmrs_spmv; variants
+ * ROW, STRIP and PADDED (explicit MERGE: CMRS_ERR_UNSUPPORTED; AUTO picks ROW
+ * where cmrs_spmv would pick MERGE).  Costs 4 bytes per row of map reads.
+ * Asynchronous. */
+int cmrs_spmv_rows(const cmrs_matrix *A, const void *x, void *y, const int32_t *row_map, int variant,
+                   void *workspace, size_t workspace_bytes, void *stream);
 
 /* SpMV that allocates nothing, for callers that cannot allocate device
  * memory at all: code that runs inside an allocator or memory-pool callback,

@@ -78,6 +78,10 @@ def lib():
             "cmrs_spmv_workspace": ([M, i, ctypes.POINTER(sz)], i),
             "cmrs_spmv_variant": ([M, i, ctypes.POINTER(ctypes.c_int)], i),
             "cmrs_pad_workspace": ([M, i, ctypes.POINTER(sz)], i),
+            "cmrs_row_order": ([i, vp, i, vp, vp], i),
+            "cmrs_permute_csr_workspace": ([i, ctypes.POINTER(sz)], i),
+            "cmrs_permute_csr": ([i, i, vp, vp, vp, i, vp, vp, vp, vp, vp, sz, vp], i),
+            "cmrs_spmv_rows": ([M, vp, vp, vp, i, vp, sz, vp], i),
             "cmrs_pad_layout": ([M, i, vp, ctypes.POINTER(ctypes.c_int32), vp, sz, vp], i),
             "cmrs_pad_fill": ([M, i, vp, ctypes.c_int32, vp, vp, vp, M], i),
             "cmrs_spmv": ([M, vp, vp, i, vp, sz, vp], i),
@@ -227,6 +231,45 @@ def cmrs_pad(A: Matrix, slots=CMRS_PAD_SLOTS, stream=None):
     _check(lib().cmrs_pad_fill(A.ref(), slots, _ptr(sp), npad, _ptr(pk), _ptr(vout), _stream(stream),
                                ctypes.byref(m)), "cmrs_pad_fill")
     return Matrix(m, sp, pk, vout)
+
+
+def cmrs_row_order(row_ptr, window, stream=None):
+    """Row reordering: perm[i] = original row at position i; rows sorted by
+    length (longest first, ties in order) inside windows of `window` rows."""
+    rows = row_ptr.numel() - 1
+    perm = torch.empty(max(rows, 1), dtype=torch.int32, device=row_ptr.device)
+    _check(lib().cmrs_row_order(rows, _ptr(row_ptr), int(window), _ptr(perm), _stream(stream)), "cmrs_row_order")
+    return perm[:rows]
+
+
+def cmrs_permute_csr(row_ptr, col_ind, val, perm, stream=None):
+    """CRS of P A (row i = original row perm[i]); val float64/float32 or None."""
+    dev = row_ptr.device
+    rows, nnz = row_ptr.numel() - 1, col_ind.numel()
+    rp = torch.empty(rows + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    vo = torch.empty(max(nnz, 1), dtype=val.dtype, device=dev) if val is not None else None
+    vdt = {torch.float64: CMRS_F64, torch.float32: CMRS_F32}[val.dtype] if val is not None else CMRS_F64
+    n = ctypes.c_size_t()
+    _check(lib().cmrs_permute_csr_workspace(rows, ctypes.byref(n)), "cmrs_permute_csr_workspace")
+    ws = workspace(n.value, dev)
+    _check(lib().cmrs_permute_csr(rows, nnz, _ptr(row_ptr), _ptr(col_ind), _ptr(val) if val is not None else None,
+                                  vdt, _ptr(perm), _ptr(rp), _ptr(ci), _ptr(vo) if vo is not None else None,
+                                  _ptr(ws), n.value, _stream(stream)), "cmrs_permute_csr")
+    return rp, ci[:nnz], (vo[:nnz] if vo is not None else None)
+
+
+def cmrs_spmv_rows(A: Matrix, x, row_map, y=None, variant=CMRS_VARIANT_AUTO, workspace_tensor=None, stream=None):
+    """y[row_map[i]] = (A x)_i: the product of a row-reordered matrix in the original order."""
+    if y is None:
+        y = torch.empty(A.rows, dtype=A.x_dtype, device=x.device)
+    v = variant
+    ws = workspace_tensor if workspace_tensor is not None else A.spmv_workspace(
+        CMRS_VARIANT_ROW if v == CMRS_VARIANT_AUTO and cmrs_spmv_variant(A, v) == CMRS_VARIANT_MERGE else v)
+    rc = lib().cmrs_spmv_rows(A.ref(), _ptr(x), _ptr(y), _ptr(row_map), variant, _ptr(ws), ws.numel(),
+                              _stream(stream))
+    _check(rc, "cmrs_spmv_rows")
+    return y
 
 
 def cmrs_spmv(A: Matrix, x, y=None, variant=CMRS_VARIANT_AUTO, workspace_tensor=None, stream=None):

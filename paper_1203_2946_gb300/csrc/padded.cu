@@ -17,14 +17,14 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "scan.cuh"
 
 namespace cmrs {
 namespace {
 
 constexpr int kPadWarps = 8;
-constexpr int kScanThreads = 1024;
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr uint32_t ST_PAD_OVERFLOW = 1u, ST_PAD_PLAN = 2u;
+constexpr uint32_t ST_PAD_PLAN = 2u;
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   int incl = v;
@@ -137,101 +137,7 @@ __global__ void __launch_bounds__(kPadWarps * 32) k_pad_fill(int strips, int hei
     pad_strip<true, S, kSplit>(s, height, bits, slots, sp, packed, vh, vl, sp_out[s], pk_out, vo_h, vo_l);
 }
 
-// ---- inclusive scan of the pass counts into the padded StripPtr
-// Block-local inclusive scan (int64) of counts, block totals into aux.
-__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(int n, const int32_t *__restrict__ in,
-                                                               long long *__restrict__ incl,
-                                                               long long *__restrict__ aux) {
-  __shared__ long long wsum[kScanThreads / 32];
-  const int i = blockIdx.x * kScanThreads + threadIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  long long v = i < n ? in[i] : 0;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const long long t = __shfl_up_sync(kFull, v, o);
-    if (lane >= o) v += t;
-  }
-  if (lane == 31) wsum[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    long long t = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long u = __shfl_up_sync(kFull, t, o);
-      if (lane >= o) t += u;
-    }
-    wsum[lane] = t;
-  }
-  __syncthreads();
-  if (w > 0) v += wsum[w - 1];
-  if (i < n) incl[i] = v;
-  if (threadIdx.x == kScanThreads - 1) aux[blockIdx.x] = v;
-}
-
-// Exclusive scan of the block totals, in place, by one block.
-__global__ void __launch_bounds__(kScanThreads) k_scan_aux(int nb, long long *__restrict__ aux) {
-  __shared__ long long wsum[kScanThreads / 32];
-  __shared__ long long carry;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
-    const int i = b0 + threadIdx.x;
-    const long long x = i < nb ? aux[i] : 0;
-    long long v = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const long long t = __shfl_up_sync(kFull, v, o);
-      if (lane >= o) v += t;
-    }
-    if (lane == 31) wsum[w] = v;
-    __syncthreads();
-    if (w == 0) {
-      long long t = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long u = __shfl_up_sync(kFull, t, o);
-        if (lane >= o) t += u;
-      }
-      wsum[lane] = t;
-    }
-    __syncthreads();
-    if (w > 0) v += wsum[w - 1];
-    const long long c = carry;
-    if (i < nb) aux[i] = c + v - x;
-    __syncthreads();
-    if (threadIdx.x == kScanThreads - 1) carry = c + v;
-    __syncthreads();
-  }
-}
-
-__global__ void k_scan_finish(int n, const long long *__restrict__ incl, const long long *__restrict__ aux,
-                              int32_t *__restrict__ sp_out, uint32_t *status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) sp_out[0] = 0;
-  if (i >= n) return;
-  const long long items = 32 * (incl[i] + aux[i / kScanThreads]);
-  if (items > 0x7fffffffLL) {
-    atomicOr(status, ST_PAD_OVERFLOW);
-    sp_out[i + 1] = 0x7fffffff;
-  } else {
-    sp_out[i + 1] = (int32_t)items;
-  }
-}
-
-struct PadLayout {
-  size_t counts, incl, aux, total;
-};
-
-PadLayout pad_layout_ws(int strips) {
-  PadLayout L;
-  const size_t nb = (size_t)ceil_div(strips > 0 ? strips : 1, kScanThreads);
-  L.counts = 256;
-  L.incl = L.counts + align256((size_t)(strips > 0 ? strips : 1) * 4);
-  L.aux = L.incl + align256((size_t)(strips > 0 ? strips : 1) * 8);
-  L.total = L.aux + align256(nb * 8);
-  return L;
-}
+size_t pad_ws_bytes(int strips) { return 256 + scan_ws_bytes(strips); }
 
 int slots_log2(int slots) {
   for (int k = 0; k <= 3; ++k)
@@ -284,7 +190,7 @@ extern "C" int cmrs_pad_workspace(const cmrs_matrix *A, int slots, size_t *bytes
   if (!bytes) return CMRS_ERR_ARG;
   const int rc = check_pad_input(A, slots);
   if (rc) return rc;
-  *bytes = pad_layout_ws(A->strips).total;
+  *bytes = pad_ws_bytes(A->strips);
   return CMRS_OK;
 }
 
@@ -293,15 +199,12 @@ extern "C" int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_p
   int rc = check_pad_input(A, slots);
   if (rc) return rc;
   if (!strip_ptr_padded || !nnz_padded) return CMRS_ERR_ARG;
-  const PadLayout L = pad_layout_ws(A->strips);
-  if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+  if (!workspace || workspace_bytes < pad_ws_bytes(A->strips) || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return CMRS_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
   char *ws = reinterpret_cast<char *>(workspace);
   uint32_t *status = reinterpret_cast<uint32_t *>(ws);
-  int32_t *counts = reinterpret_cast<int32_t *>(ws + L.counts);
-  long long *incl = reinterpret_cast<long long *>(ws + L.incl);
-  long long *aux = reinterpret_cast<long long *>(ws + L.aux);
+  int32_t *counts = reinterpret_cast<int32_t *>(ws + 256);
   CMRS_CUDA_TRY(cudaMemsetAsync(status, 0, 4, st));
   const int S = A->strips;
   if (S == 0) {
@@ -313,19 +216,14 @@ extern "C" int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_p
   k_pad_count<<<pad_grid(S), kPadWarps * 32, 0, st>>>(S, A->height, A->bits, slots, A->strip_ptr, A->col_packed,
                                                       counts, status);
   CMRS_LAUNCH_CHECK();
-  const int nb = (int)ceil_div(S, kScanThreads);
-  k_scan_blocks<<<nb, kScanThreads, 0, st>>>(S, counts, incl, aux);
-  CMRS_LAUNCH_CHECK();
-  k_scan_aux<<<1, kScanThreads, 0, st>>>(nb, aux);
-  CMRS_LAUNCH_CHECK();
-  k_scan_finish<<<(int)ceil_div(S, 256), 256, 0, st>>>(S, incl, aux, strip_ptr_padded, status);
-  CMRS_LAUNCH_CHECK();
+  rc = scan_counts(S, ws + 256, 32, strip_ptr_padded, status, st);
+  if (rc) return rc;
   uint32_t host[2] = {0, 0};
   CMRS_CUDA_TRY(cudaMemcpyAsync(&host[0], status, 4, cudaMemcpyDeviceToHost, st));
   CMRS_CUDA_TRY(cudaMemcpyAsync(&host[1], strip_ptr_padded + S, 4, cudaMemcpyDeviceToHost, st));
   CMRS_CUDA_TRY(cudaStreamSynchronize(st));
   if (host[0] & ST_PAD_PLAN) return CMRS_ERR_CSR_INVALID;
-  if (host[0] & ST_PAD_OVERFLOW) return CMRS_ERR_ARG;
+  if (host[0] & ST_SCAN_OVERFLOW) return CMRS_ERR_ARG;
   *nnz_padded = (int32_t)host[1];
   return CMRS_OK;
 }

@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int
                                                                    const typename Form<DT>::Stored *__restrict__ lo,
                                                                    const typename Form<DT>::Acc *__restrict__ x,
                                                                    typename Form<DT>::Acc *__restrict__ y,
+                                                                   const int32_t *__restrict__ row_map,
                                                                    uint32_t *status) {
   typedef typename Form<DT>::Stored S;
   typedef typename Form<DT>::Acc A;
@@ -318,7 +319,10 @@ __global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int
       const A other = __shfl_down_sync(0xffffffffu, acc, o);
       if (q < o) acc += other;
     }
-    if (run && q == 0) y[row] = acc;
+    if (run && q == 0) {
+      const long long t = row_map ? row_map[row] : row;  // y position (row map of a reordered matrix)
+      if (t >= 0 && t < rows) y[t] = acc;
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
     if (!ok) break;
@@ -338,7 +342,8 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_spmv_strip(int rows, int h
                                                                   const typename Form<DT>::Stored *__restrict__ hi,
                                                                   const typename Form<DT>::Stored *__restrict__ lo,
                                                                   const typename Form<DT>::Acc *__restrict__ x,
-                                                                  typename Form<DT>::Acc *__restrict__ y) {
+                                                                  typename Form<DT>::Acc *__restrict__ y,
+                                                                  const int32_t *__restrict__ row_map) {
   typedef typename Form<DT>::Acc A;
   extern __shared__ __align__(128) char smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -367,7 +372,10 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_spmv_strip(int rows, int h
     }
     if (lane < height) {
       const long long row = (long long)s * height + lane;
-      if (row < rows) y[row] = buf[lane * 32];
+      if (row < rows) {
+        const long long t = row_map ? row_map[row] : row;
+        if (t >= 0 && t < rows) y[t] = buf[lane * 32];
+      }
     }
     __syncwarp();
   }
@@ -416,7 +424,8 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
                                                                const typename Form<DT>::Stored *__restrict__ hi,
                                                                const typename Form<DT>::Stored *__restrict__ lo,
                                                                const typename Form<DT>::Acc *__restrict__ x,
-                                                               typename Form<DT>::Acc *__restrict__ y) {
+                                                               typename Form<DT>::Acc *__restrict__ y,
+                                                               const int32_t *__restrict__ row_map) {
   typedef typename Form<DT>::Acc A;
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -463,7 +472,10 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
     }
     const long long row0 = (long long)s * height;
     if (kM == 1) {
-      if (row0 + lane < rows) y[row0 + lane] = acc;
+      if (row0 + lane < rows) {
+        const long long t = row_map ? row_map[row0 + lane] : row0 + lane;
+        if (t >= 0 && t < rows) y[t] = acc;
+      }
     } else {
       __syncwarp();
       const int r = lane / G, part = lane - r * G;
@@ -474,7 +486,10 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
         for (int m = 1; m < per; ++m) sum += q[m];
       }
       for (int o = G >> 1; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if (part == 0 && r < height && row0 + r < rows) y[row0 + r] = sum;
+      if (part == 0 && r < height && row0 + r < rows) {
+        const long long t = row_map ? row_map[row0 + r] : row0 + r;
+        if (t >= 0 && t < rows) y[t] = sum;
+      }
       __syncwarp();
     }
   }
@@ -787,7 +802,8 @@ size_t merge_ws_bytes(int nnz) {
 
 template <int DT, int kM>
 int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, const typename Form<DT>::Stored *lo,
-                  const typename Form<DT>::Acc *x, typename Form<DT>::Acc *y, cudaStream_t st) {
+                  const typename Form<DT>::Acc *x, typename Form<DT>::Acc *y, const int32_t *row_map,
+                  cudaStream_t st) {
   typedef typename Form<DT>::Acc Acc;
   static Occ occ;
   const size_t smem = (size_t)kPadWarps * kM * A->height * sizeof(Acc);
@@ -795,13 +811,14 @@ int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, con
   const long long need = ceil_div(A->strips, kPadWarps);
   const int grid = (int)std::min<long long>(need, (long long)per_sm * sm_count());
   k_spmv_padded<DT, kM><<<grid, kPadWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->strip_ptr,
-                                                             A->col_packed, hi, lo, x, y);
+                                                             A->col_packed, hi, lo, x, y, row_map);
   CMRS_LAUNCH_CHECK();
   return CMRS_OK;
 }
 
 template <int DT>
-int launch(const cmrs_matrix *A, const void *xv, void *yv, int variant, char *ws, cudaStream_t st) {
+int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_map, int variant, char *ws,
+           cudaStream_t st) {
   typedef typename Form<DT>::Stored S;
   typedef typename Form<DT>::Acc Acc;
   const S *hi = reinterpret_cast<const S *>(A->val);
@@ -817,7 +834,7 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, int variant, char *ws
     const long long nblk = ceil_div(A->rows, kRowThreads);
     const int grid = (int)std::min<long long>(nblk, (long long)per_sm * sms);
     k_spmv_row<DT><<<grid, RowCfg<DT>::kThreads, smem, st>>>(A->rows, A->height, A->bits, A->nnz, A->strip_ptr,
-                                                             A->col_packed, hi, lo, x, y, status);
+                                                             A->col_packed, hi, lo, x, y, row_map, status);
     CMRS_LAUNCH_CHECK();
   } else if (variant == CMRS_VARIANT_STRIP) {
     static Occ occ;
@@ -826,14 +843,14 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, int variant, char *ws
     const long long need = ceil_div(A->strips, kStripWarps);
     const int grid = (int)std::min<long long>(need, (long long)per_sm * sms);
     k_spmv_strip<DT><<<grid, kStripWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->strip_ptr,
-                                                           A->col_packed, hi, lo, x, y);
+                                                           A->col_packed, hi, lo, x, y, row_map);
     CMRS_LAUNCH_CHECK();
   } else if (variant == CMRS_VARIANT_PADDED) {
     switch (CMRS_PAD_SLOTS_OF(A->flags)) {
-      case 1: return launch_padded<DT, 1>(A, hi, lo, x, y, st);
-      case 2: return launch_padded<DT, 2>(A, hi, lo, x, y, st);
-      case 4: return launch_padded<DT, 4>(A, hi, lo, x, y, st);
-      default: return launch_padded<DT, 8>(A, hi, lo, x, y, st);
+      case 1: return launch_padded<DT, 1>(A, hi, lo, x, y, row_map, st);
+      case 2: return launch_padded<DT, 2>(A, hi, lo, x, y, row_map, st);
+      case 4: return launch_padded<DT, 4>(A, hi, lo, x, y, row_map, st);
+      default: return launch_padded<DT, 8>(A, hi, lo, x, y, row_map, st);
     }
   } else {
     static Occ occ;
@@ -925,13 +942,22 @@ extern "C" int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *by
   return CMRS_OK;
 }
 
-extern "C" int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant, void *workspace,
-                         size_t workspace_bytes, void *stream) {
+namespace cmrs {
+namespace {
+
+// y[map[i]] = (A x)_i, map NULL for the identity.  With a map, AUTO never
+// picks MERGE (whose rows leave through several paths) but ROW instead.
+int spmv_impl(const cmrs_matrix *A, const void *x, void *y, const int32_t *row_map, int variant, void *workspace,
+              size_t workspace_bytes, void *stream) {
   int rc = check_matrix(A);
   if (rc) return rc;
   int v = 0;
   rc = resolve_variant(A, variant, &v);
   if (rc) return rc;
+  if (row_map && v == CMRS_VARIANT_MERGE) {
+    if (variant != CMRS_VARIANT_AUTO) return CMRS_ERR_UNSUPPORTED;
+    v = CMRS_VARIANT_ROW;
+  }
   if (A->rows == 0) return CMRS_OK;
   if (!y || (A->nnz > 0 && !x)) return CMRS_ERR_ARG;
   const size_t need = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz) : 256;
@@ -948,12 +974,26 @@ extern "C" int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int varia
   }
   char *ws = reinterpret_cast<char *>(workspace);
   switch (A->dtype) {
-    case CMRS_F64: return launch<CMRS_F64>(A, x, y, v, ws, st);
-    case CMRS_F32: return launch<CMRS_F32>(A, x, y, v, ws, st);
-    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, v, ws, st);
-    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, v, ws, st);
+    case CMRS_F64: return launch<CMRS_F64>(A, x, y, row_map, v, ws, st);
+    case CMRS_F32: return launch<CMRS_F32>(A, x, y, row_map, v, ws, st);
+    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, row_map, v, ws, st);
+    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, row_map, v, ws, st);
   }
   return CMRS_ERR_ARG;
+}
+
+}  // namespace
+}  // namespace cmrs
+
+extern "C" int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant, void *workspace,
+                         size_t workspace_bytes, void *stream) {
+  return spmv_impl(A, x, y, nullptr, variant, workspace, workspace_bytes, stream);
+}
+
+extern "C" int cmrs_spmv_rows(const cmrs_matrix *A, const void *x, void *y, const int32_t *row_map, int variant,
+                              void *workspace, size_t workspace_bytes, void *stream) {
+  if (!row_map && A && A->rows > 0) return CMRS_ERR_ARG;
+  return spmv_impl(A, x, y, row_map, variant, workspace, workspace_bytes, stream);
 }
 
 extern "C" int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, void *stream) {
@@ -1022,10 +1062,10 @@ extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, v
   CMRS_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, st));
   char *ws = reinterpret_cast<char *>(scratch);
   switch (A->dtype) {
-    case CMRS_F64: return launch<CMRS_F64>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
-    case CMRS_F32: return launch<CMRS_F32>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
-    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
-    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_F64: return launch<CMRS_F64>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_F32: return launch<CMRS_F32>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
   }
   return CMRS_ERR_ARG;
 }

@@ -364,3 +364,12 @@ def dense_as_sparse(n: int = 10_000, seed: int = 8) -> CSR:
     (r,) = _streams(seed, 1)
     col = np.tile(np.arange(n, dtype=np.int32), n)
     return _finish(n, n, np.full(n, n, np.int64), col, r.uniform(-1.0, 1.0, n * n), "dense%d" % n)
+
+
+def workload_irregular(n: int = 2_097_152, seed: int = 3):
+    """Moderately irregular rows for row reordering: banded random, window
+    2048, lengths U{4..60} (mean 32), values N(0, 1) as FP64, x ~ U[-1, 1]
+    (seed 0)."""
+    a = banded_random(n, 2048, 4, 60, seed)
+    a = CSR(a.rows, a.cols, a.row_ptr, a.col_ind, a.val.astype(np.float64), "irregular_n%d" % n)
+    return a, uniform_vector(a.cols, 0)

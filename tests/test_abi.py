@@ -137,3 +137,20 @@ def test_pad_host_validation(L):
     m.flags, m.height, m.strips = 0, 2, 50
     assert L.cmrs_pad_workspace(ctypes.byref(m), 8, ctypes.byref(n)) == 2   # 2 x 8 slots < 32 lanes
     assert L.cmrs_pad_workspace(None, 8, ctypes.byref(n)) == 1
+
+
+def test_reorder_host_validation(L):
+    """Row reordering entry points: argument checks made on the host."""
+    p = ctypes.c_void_p(256)
+    assert L.cmrs_row_order(10, p, 0, p, None) == 1       # window below 1
+    assert L.cmrs_row_order(10, p, 4097, p, None) == 1    # window above 4096
+    assert L.cmrs_row_order(0, None, 32, None, None) == 0  # nothing to order
+    n = ctypes.c_size_t()
+    assert L.cmrs_permute_csr_workspace(1000, ctypes.byref(n)) == 0 and n.value >= 256 + 4000
+    assert L.cmrs_permute_csr(10, 5, p, p, p, 2, p, p, p, p, p, 1 << 20, None) == 1   # BF16 input values
+    assert L.cmrs_permute_csr(10, 5, p, p, None, 0, p, p, p, None, None, 0, None) == 7  # no workspace
+    from paper_1203_2946_gb300 import binding as b
+    m = b.cmrs_matrix()
+    m.rows, m.cols, m.nnz, m.height, m.strips, m.bits, m.dtype = 10, 10, 5, 4, 3, 4, 0
+    m.strip_ptr = m.col_packed = m.val = 256
+    assert L.cmrs_spmv_rows(ctypes.byref(m), p, p, None, -1, p, 1 << 20, None) == 1   # no row map
