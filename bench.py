@@ -11,9 +11,11 @@ of CUDA events on the launching stream.
 Metric: GB/s = beta_plus / t with beta_plus = (s_v + s_i) nnz + s_i strips +
 2 s_v rows (Eq. 6.1: matrix, x and y moved once), also GFLOP/s = 2 nnz / t and
 the paper's (2 nnz - rows) / t.  e2e: the same metric through the C ABI with x
-copied from pinned host memory and y copied back inside the timed region.
+copied from pinned host memory and y copied back inside the timed region,
+every step, neighbouring steps' copies overlapping the product on two
+buffer pairs.
 
-  python bench.py [--steps K] [--warmup W] [--height H] [--variant row|strip|merge]
+  python bench.py [--steps K] [--warmup W] [--height H] [--variant row|strip|merge|padded|auto] [--slots M]
   python bench.py --impl reference      # the CPU oracle on the same workload
   torchrun --nproc-per-node N bench.py --gpus N   # N independent replicas
 """
@@ -265,6 +267,55 @@ def traffic_record(kernel, workload):
         return None
 
 
+def e2e_pipelined(run, xh, xds, yds, yhs, steps, warm=3):
+    """End-to-end rate through host buffers: every step copies its x from
+    pinned host memory (H2D stream), runs the product (launching stream) and
+    copies its y back to pinned host memory (D2H stream).  Two device buffer
+    pairs let one step's copy-in and the previous step's copy-out overlap a
+    product; event waits keep each buffer's reuse in order.  Returns ms per
+    step from CUDA events spanning the first copy-in to the last copy-out.
+    No L2 flush: the resident matrix is larger than L2."""
+    import torch
+    comp = torch.cuda.current_stream()
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    k_done = [torch.cuda.Event() for _ in range(2)]
+    in_done = [torch.cuda.Event() for _ in range(2)]
+    out_done = [torch.cuda.Event() for _ in range(2)]
+    count = [0]
+
+    def one():
+        i = count[0]
+        count[0] += 1
+        s = i & 1
+        if i >= 2:
+            h2d.wait_event(k_done[s])      # the product two steps back has read xds[s]
+        with torch.cuda.stream(h2d):
+            xds[s].copy_(xh, non_blocking=True)
+        in_done[s].record(h2d)
+        comp.wait_event(in_done[s])
+        if i >= 2:
+            comp.wait_event(out_done[s])   # yds[s] was copied out two steps back
+        run(xds[s], yds[s])
+        k_done[s].record(comp)
+        d2h.wait_event(k_done[s])
+        with torch.cuda.stream(d2h):
+            yhs[s].copy_(yds[s], non_blocking=True)
+        out_done[s].record(d2h)
+
+    for _ in range(warm):
+        one()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(h2d)
+    for _ in range(steps):
+        one()
+    comp.wait_event(out_done[(count[0] - 1) & 1])
+    comp.wait_event(out_done[count[0] & 1])
+    end.record(comp)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / steps
+
+
 def time_steps(fn, steps, flush, stream):
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -330,20 +381,14 @@ def run_ours(args):
     value = world * bp * args.steps / (total_ms / 1e3) / 1e9
     b.cmrs_spmv_check(M, variant)
 
-    # e2e through the C ABI with host buffers
+    # e2e through the C ABI with host buffers (x in, y out every step, pipelined)
     xh = torch.from_numpy(x).pin_memory()
-    yh = torch.empty(a.rows, dtype=torch.float64).pin_memory()
-
-    def e2e_step():
-        xd.copy_(xh, non_blocking=True)
-        b.cmrs_spmv(M, xd, yd, binding_variant, ws)
-        yh.copy_(yd, non_blocking=True)
-
+    yhs = [torch.empty(a.rows, dtype=torch.float64).pin_memory() for _ in range(2)]
+    xds = [xd, torch.empty_like(xd)]
+    yds = [yd, torch.empty_like(yd)]
     e2e_steps = max(20, min(args.steps, 200))
-    for _ in range(3):
-        e2e_step()
-    e2e_times = time_steps(e2e_step, e2e_steps, flush, stream)
-    e2e_ms = max_over_ranks(dist, statistics.mean(e2e_times))
+    e2e_ms = max_over_ranks(dist, e2e_pipelined(lambda xv, yv: b.cmrs_spmv(M, xv, yv, binding_variant, ws), xh, xds,
+                                                yds, yhs, e2e_steps))
 
     kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[variant]
     trimmed = sorted(times)[:-1] if len(times) > 1 else times
@@ -372,7 +417,9 @@ def run_ours(args):
                          "_m%d" % args.slots if args.variant == "padded" else "")), "kernel": kname},
         "e2e": {"value": world * bp / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(a.rows * 8),
-                "ms_per_step": e2e_ms, "note": "x host->device, cmrs_spmv, y device->host; matrix resident"},
+                "ms_per_step": e2e_ms, "note": "x host->device, cmrs_spmv, y device->host every step, "
+                "pipelined over two buffer pairs (copy-in, product and copy-out of neighbouring steps overlap); "
+                "matrix resident"},
         "gpu_launches": args.steps * (3 if variant == 2 else 1),
         "clocks": sampler.summary(),
         "wall_s_timed_region": wall,
@@ -636,15 +683,9 @@ def run_secondary(args):
                 var[vn] = {"ms": vms, "gbs": bp / (vms / 1e3) / 1e9}
             extra["variants_f32"] = var
         xh = torch.from_numpy(x).pin_memory()
-        yh = torch.empty(a.rows, dtype=xd.dtype).pin_memory()
-
-        def e2e():
-            xd.copy_(xh, non_blocking=True)
-            fn()
-            yh.copy_(yd, non_blocking=True)
-        for _ in range(3):
-            e2e()
-        e_ms = statistics.mean(time_steps(e2e, max(20, min(steps, 200)), flush, stream))
+        yhs = [torch.empty(a.rows, dtype=xd.dtype).pin_memory() for _ in range(2)]
+        e_ms = e2e_pipelined(lambda xv, yv: b.cmrs_spmv(M, xv, yv, v, ws), xh, [xd, torch.empty_like(xd)],
+                             [yd, torch.empty_like(yd)], yhs, max(20, min(steps, 200)))
         kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[ran]
         line = _line(args, gbs, "GB/s", per_ms, name,
                      {"workload": wl, "height": h, "variant": args.variant,
@@ -838,15 +879,13 @@ def run_irregular(args):
         ms = timed(f)
         others[name] = {"ms": ms, "gbs": bp / (ms / 1e3) / 1e9, "stored_items_per_nnz": mat.nnz / a.nnz}
     xh = torch.from_numpy(x).pin_memory()
-    yh = torch.empty(a.rows, dtype=torch.float64).pin_memory()
-
-    def e2e():
-        xd.copy_(xh, non_blocking=True)
-        fn()
-        yh.copy_(yd, non_blocking=True)
-    for _ in range(3):
-        e2e()
-    e_ms = statistics.mean(time_steps(e2e, max(20, min(steps, 200)), flush, stream))
+    yhs = [torch.empty(a.rows, dtype=torch.float64).pin_memory() for _ in range(2)]
+    if perm is None:
+        run = lambda xv, yv: b.cmrs_spmv(P, xv, yv, b.CMRS_VARIANT_PADDED, ws)  # noqa: E731
+    else:
+        run = lambda xv, yv: b.cmrs_spmv_rows(P, xv, perm, yv, b.CMRS_VARIANT_PADDED, ws)  # noqa: E731
+    e_ms = e2e_pipelined(run, xh, [xd, torch.empty_like(xd)], [yd, torch.empty_like(yd)], yhs,
+                         max(20, min(steps, 200)))
     extra = {"gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9, "eta": eta(a.nnz, a.rows, S, 8, per_ms, peak),
              "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))},
              "reorder_pad_prep_ms": prep_ms, "others": others}
