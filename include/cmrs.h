@@ -333,11 +333,13 @@ int cmrs_spmm_autotune(int batch, const cmrs_matrix *const *A, const int32_t *k,
  * Section 6.7 measures what per-matrix tuning gains.  The selector predicts
  * (height, variant) from CMRS_NFEAT features of the CRS matrix with a small
  * MLP (CMRS_NFEAT -> nh -> nh -> CMRS_SEL_CHOICES, ReLU), trained on this
- * library's own timings by the kernels below.  Choice c means height
- * {1,2,4,8,16,32}[c / 3] and variant c % 3; the network outputs a predicted
- * cost per choice and the smallest wins. */
+ * library's own timings by the kernels below.  Choice c < 18 means plain
+ * CMRS with height {1,2,4,8,16,32}[c / 3] and variant c % 3; choices 18, 19
+ * and 20 mean the modified CMRS of Section 6.6 (variant CMRS_VARIANT_PADDED)
+ * at (height, slots) = (32, 1), (32, 2) and (16, 8).  The network outputs a
+ * predicted cost per choice and the smallest wins. */
 #define CMRS_NFEAT 24
-#define CMRS_SEL_CHOICES 18
+#define CMRS_SEL_CHOICES 21
 
 /* Features (device double[CMRS_NFEAT]) of a CRS matrix (device row_ptr,
  * col_ind), from exact integer sums: log2 rows, log2 nnz, log2(1+mu), row
@@ -371,14 +373,18 @@ typedef struct cmrs_selector {
   const float *feat_scale;
 } cmrs_selector;
 
-/* Picks (height, variant) for a CRS matrix.  model != NULL: features +
- * network + argmin on the device.  model == NULL: exhaustive autotune,
- * converting with every height and timing every variant (5 timed calls
- * each) on FP32 copies held in the workspace.  Synchronises `stream`. */
+/* Picks (height, variant, slots) for a CRS matrix: *slots_out is 0 for
+ * plain CMRS, else the slots of the padded form (variant
+ * CMRS_VARIANT_PADDED).  model != NULL: features + network + argmin on the
+ * device.  model == NULL: exhaustive autotune, converting with every height
+ * and timing every variant and the three padded forms (5 timed calls each)
+ * on FP32 copies held in the workspace; a padded form with more than
+ * 2 * nnz + 32 * (rows / 16 + 2) items is not timed.  Synchronises
+ * `stream`. */
 int cmrs_select_strip_workspace(int rows, int cols, int nnz, int exhaustive, size_t *bytes);
 int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row_ptr, const int32_t *col_ind,
-                      const cmrs_selector *model, int *height_out, int *variant_out, void *workspace,
-                      size_t workspace_bytes, void *stream);
+                      const cmrs_selector *model, int *height_out, int *variant_out, int *slots_out,
+                      void *workspace, size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -51,7 +51,8 @@ class cmrs_selector(ctypes.Structure):
 
 NFEAT = 24
 SEL_HEIGHTS = (1, 2, 4, 8, 16, 32)
-SEL_CHOICES = 18
+SEL_PADDED = ((32, 1), (32, 2), (16, 8))  # choices 18..20: modified CMRS (height, slots)
+SEL_CHOICES = 18 + len(SEL_PADDED)
 
 _lib = None
 
@@ -104,7 +105,7 @@ def lib():
                                ctypes.c_float, vp], i),
             "cmrs_select_strip_workspace": ([i, i, i, i, ctypes.POINTER(sz)], i),
             "cmrs_select_strip": ([i, i, i, vp, vp, ctypes.POINTER(cmrs_selector), ctypes.POINTER(i),
-                                   ctypes.POINTER(i), vp, sz, vp], i),
+                                   ctypes.POINTER(i), ctypes.POINTER(i), vp, sz, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -449,8 +450,9 @@ def cmrs_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-
 
 
 def cmrs_select_strip(row_ptr, col_ind, cols, model=None, stream=None):
-    """(height, variant) for a CRS matrix; model: dict(params, mean, scale, nh)
-    of device tensors, or None for the exhaustive autotune."""
+    """(height, variant, slots) for a CRS matrix (slots 0: plain CMRS);
+    model: dict(params, mean, scale, nh) of device tensors, or None for the
+    exhaustive autotune."""
     rows = row_ptr.numel() - 1
     nnz = col_ind.numel()
     n = ctypes.c_size_t()
@@ -461,8 +463,8 @@ def cmrs_select_strip(row_ptr, col_ind, cols, model=None, stream=None):
     if model is not None:
         sel = cmrs_selector(NFEAT, int(model["nh"]), SEL_CHOICES, model["params"].data_ptr(),
                             model["mean"].data_ptr(), model["scale"].data_ptr())
-    h, v = ctypes.c_int(), ctypes.c_int()
+    h, v, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().cmrs_select_strip(rows, cols, nnz, _ptr(row_ptr), _ptr(col_ind),
                                    ctypes.byref(sel) if sel is not None else None, ctypes.byref(h), ctypes.byref(v),
-                                   _ptr(ws), n.value, _stream(stream)), "cmrs_select_strip")
-    return h.value, v.value
+                                   ctypes.byref(m), _ptr(ws), n.value, _stream(stream)), "cmrs_select_strip")
+    return h.value, v.value, m.value

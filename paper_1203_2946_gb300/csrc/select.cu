@@ -15,6 +15,8 @@ namespace {
 
 constexpr int kNFeat = 24;
 constexpr int kHeights[6] = {1, 2, 4, 8, 16, 32};
+// choices 18, 19, 20: the modified CMRS of Section 6.6 at (height, slots)
+constexpr int kPadChoice[3][2] = {{32, 1}, {32, 2}, {16, 8}};
 
 struct FeatAcc {
   unsigned long long sum_l2, max_l, empty, same, near, sum_d, max_d;
@@ -356,6 +358,10 @@ extern "C" int cmrs_mlp_adam(int n, float *params, const float *grads, float *m,
 }
 
 // ------------------------------------------------------------------ selection
+// Padded forms the exhaustive sweep times must fit this many items; a form
+// padded beyond it (more than twice the entries) is not a candidate.
+static size_t pad_cap(int rows, int nnz) { return 2 * (size_t)nnz + 32 * ((size_t)rows / 16 + 2); }
+
 static size_t select_ws(int rows, int cols, int nnz, int exhaustive) {
   size_t b = features_ws(rows) + align256(kNFeat * 8) + align256(1024 * 4) + align256(64);
   if (exhaustive) {
@@ -365,6 +371,9 @@ static size_t select_ws(int rows, int cols, int nnz, int exhaustive) {
     size_t s = 0;
     cmrs_from_csr_workspace(rows, nnz, 1, 0, CMRS_F32, &s);
     b += align256(s);
+    // padded forms: StripPtr, items (packed + FP32 values) and the layout pass's workspace
+    b += align256(((size_t)rows / 16 + 2) * 4) + 2 * align256(pad_cap(rows, nnz) * 4) + align256(256) +
+         align256(((size_t)rows / 16 + 2) * 4) + align256(((size_t)rows / 16 + 2) * 8) + align256(((size_t)rows / 16 / 1024 + 2) * 8);
     b += align256(256 + ((size_t)nnz / 1920 + 2) * 40 + 4096);
   }
   return b;
@@ -382,9 +391,9 @@ __global__ void k_fill(float *p, long long n, float v) {
 }
 
 extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row_ptr, const int32_t *col_ind,
-                                 const cmrs_selector *model, int *height_out, int *variant_out, void *workspace,
-                                 size_t workspace_bytes, void *stream) {
-  if (rows < 1 || cols < 1 || nnz < 0 || !row_ptr || !height_out || !variant_out) return CMRS_ERR_ARG;
+                                 const cmrs_selector *model, int *height_out, int *variant_out, int *slots_out,
+                                 void *workspace, size_t workspace_bytes, void *stream) {
+  if (rows < 1 || cols < 1 || nnz < 0 || !row_ptr || !height_out || !variant_out || !slots_out) return CMRS_ERR_ARG;
   const int exhaustive = model == nullptr;
   const size_t need = select_ws(rows, cols, nnz, exhaustive);
   if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CMRS_ERR_WORKSPACE;
@@ -398,13 +407,13 @@ extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row
   int *choice = reinterpret_cast<int *>(ws + off);
   off += align256(64);
   if (!exhaustive) {
-    if (model->nin != kNFeat || model->nout != 3 * 6 || model->nh < 1 || model->nh > 64 || !model->params ||
+    if (model->nin != kNFeat || model->nout != CMRS_SEL_CHOICES || model->nh < 1 || model->nh > 64 || !model->params ||
         !model->feat_mean || !model->feat_scale)
       return CMRS_ERR_ARG;
     int rc = cmrs_features(rows, nnz, row_ptr, col_ind, feat, workspace, features_ws(rows), stream);
     if (rc) return rc;
     const int nh = model->nh, nout = model->nout;
-    float *x = buf, *acts = buf + 32;  // 4*nh + nout <= 4*64 + 18 floats fit in the 992 left
+    float *x = buf, *acts = buf + 32;  // 4*nh + nout <= 4*64 + 21 floats fit in the 992 left
     k_normalize<<<1, 32, 0, st>>>(kNFeat, feat, model->feat_mean, model->feat_scale, x);
     rc = cmrs_mlp_forward(1, kNFeat, nh, nout, x, model->params, acts, stream);
     if (rc) return rc;
@@ -413,8 +422,15 @@ extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row
     int c = 0;
     CMRS_CUDA_TRY(cudaMemcpyAsync(&c, choice, sizeof(int), cudaMemcpyDeviceToHost, st));
     CMRS_CUDA_TRY(cudaStreamSynchronize(st));
-    *height_out = kHeights[c / 3];
-    *variant_out = c % 3;
+    if (c < 18) {
+      *height_out = kHeights[c / 3];
+      *variant_out = c % 3;
+      *slots_out = 0;
+    } else {
+      *height_out = kPadChoice[c - 18][0];
+      *variant_out = CMRS_VARIANT_PADDED;
+      *slots_out = kPadChoice[c - 18][1];
+    }
     return CMRS_OK;
   }
   // Exhaustive autotune (Section 6.2's brute force): convert with every
@@ -436,6 +452,17 @@ extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row
   cmrs_from_csr_workspace(rows, nnz, 1, 0, CMRS_F32, &cws);
   char *conv_ws = ws + off;
   off += align256(cws);
+  const size_t cap = pad_cap(rows, nnz);
+  int32_t *psp = reinterpret_cast<int32_t *>(ws + off);
+  off += align256(((size_t)rows / 16 + 2) * 4);
+  uint32_t *ppk = reinterpret_cast<uint32_t *>(ws + off);
+  off += align256(cap * 4);
+  float *pval = reinterpret_cast<float *>(ws + off);
+  off += align256(cap * 4);
+  char *pad_ws = ws + off;
+  const size_t pad_ws_bytes = align256(256) + align256(((size_t)rows / 16 + 2) * 4) +
+                              align256(((size_t)rows / 16 + 2) * 8) + align256(((size_t)rows / 16 / 1024 + 2) * 8);
+  off += pad_ws_bytes;
   char *spmv_ws = ws + off;
   const size_t spmv_bytes = workspace_bytes - off;
   k_fill<<<grid_for(std::max(nnz, 1), 256), 256, 0, st>>>(ones, std::max(nnz, 1), 1.f);
@@ -446,24 +473,37 @@ extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row
   CMRS_CUDA_TRY(cudaEventCreate(&e0));
   CMRS_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bh = 4, bv = 0, rc = CMRS_OK;
+  int bh = 4, bv = 0, bm = 0, rc = CMRS_OK;
+  auto time_one = [&](const cmrs_matrix *M, int v, int h, int m) {
+    for (int w = 0; w < 2 && rc == CMRS_OK; ++w) rc = cmrs_spmv(M, x, y, v, spmv_ws, spmv_bytes, stream);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 5 && rc == CMRS_OK; ++r) rc = cmrs_spmv(M, x, y, v, spmv_ws, spmv_bytes, stream);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess && rc == CMRS_OK) rc = set_cuda_error(e);
+    if (rc == CMRS_OK && ms < best) {
+      best = ms;
+      bh = h;
+      bv = v;
+      bm = m;
+    }
+  };
   for (int hi = 0; hi < 6 && rc == CMRS_OK; ++hi) {
     cmrs_matrix A;
     rc = cmrs_from_csr(rows, cols, nnz, row_ptr, col_ind, ones, CMRS_F32, kHeights[hi], 0, CMRS_F32, sp, pk, val,
                        conv_ws, cws, stream, &A);
-    for (int v = 0; v < 3 && rc == CMRS_OK; ++v) {
-      for (int w = 0; w < 2 && rc == CMRS_OK; ++w) rc = cmrs_spmv(&A, x, y, v, spmv_ws, spmv_bytes, stream);
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < 5 && rc == CMRS_OK; ++r) rc = cmrs_spmv(&A, x, y, v, spmv_ws, spmv_bytes, stream);
-      cudaEventRecord(e1, st);
-      cudaError_t e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess && rc == CMRS_OK) rc = set_cuda_error(e);
-      if (rc == CMRS_OK && ms < best) {
-        best = ms;
-        bh = kHeights[hi];
-        bv = v;
+    for (int v = 0; v < 3 && rc == CMRS_OK; ++v) time_one(&A, v, kHeights[hi], 0);
+    // the padded forms built from this height's CMRS
+    for (int j = 0; j < 3 && rc == CMRS_OK; ++j) {
+      if (kPadChoice[j][0] != kHeights[hi]) continue;
+      int32_t npad = 0;
+      rc = cmrs_pad_layout(&A, kPadChoice[j][1], psp, &npad, pad_ws, pad_ws_bytes, stream);
+      if (rc == CMRS_OK && (size_t)npad <= cap) {
+        cmrs_matrix P;
+        rc = cmrs_pad_fill(&A, kPadChoice[j][1], psp, npad, ppk, pval, stream, &P);
+        if (rc == CMRS_OK) time_one(&P, CMRS_VARIANT_PADDED, kHeights[hi], kPadChoice[j][1]);
       }
     }
   }
@@ -472,5 +512,6 @@ extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row
   if (rc) return rc;
   *height_out = bh;
   *variant_out = bv;
+  *slots_out = bm;
   return CMRS_OK;
 }

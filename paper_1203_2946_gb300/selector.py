@@ -8,10 +8,11 @@ the choice from 24 structural features.  Every numeric step -- features,
 conversion, SpMV timing, the network's forward and backward passes and the
 Adam updates -- runs in libcmrs kernels; this module only orchestrates.
 
-Choice c = 3 * height_index + variant, height_index over (1, 2, 4, 8, 16, 32),
-variant 0 ROW, 1 STRIP, 2 MERGE.  The network regresses the cost of every
-choice relative to the best one, log2(t_c / t_best), and the smallest
-predicted cost wins.
+Choice c < 18: plain CMRS, c = 3 * height_index + variant, height_index over
+(1, 2, 4, 8, 16, 32), variant 0 ROW, 1 STRIP, 2 MERGE.  Choices 18, 19, 20:
+the modified CMRS of Section 6.6 at (height, slots) = (32, 1), (32, 2),
+(16, 8).  The network regresses the cost of every choice relative to the
+best one, log2(t_c / t_best), and the smallest predicted cost wins.
 """
 from __future__ import annotations
 
@@ -33,7 +34,13 @@ NH = 64
 FORMAT_VERSION = 1
 
 
+PADDED = b.SEL_PADDED
+PAD_LIMIT = 2.0  # padded forms with more than twice the entries are not timed
+
+
 def choice_name(c):
+    if c >= 18:
+        return "h=%d/padded-m%d" % PADDED[c - 18]
     return "h=%d/%s" % (HEIGHTS[c // 3], ("row", "strip", "merge")[c % 3])
 
 
@@ -73,7 +80,18 @@ def time_all_choices(a: inputs.CSR, timer: Timer, device, reps=5):
         for v in range(3):
             ws = M.spmv_workspace(v)
             out[3 * hi + v] = timer.time(lambda: b.cmrs_spmv(M, x, y, v, ws), reps=reps)
+        for j, (ph, m) in enumerate(PADDED):
+            if ph != h:
+                continue
+            P = b.cmrs_pad(M, m)
+            if P.nnz > PAD_LIMIT * a.nnz + 32 * (a.rows // 16 + 2):
+                out[18 + j] = -1.0  # not timed; set below
+            else:
+                ws = P.spmv_workspace(b.CMRS_VARIANT_PADDED)
+                out[18 + j] = timer.time(lambda: b.cmrs_spmv(P, x, y, b.CMRS_VARIANT_PADDED, ws), reps=reps)
+            del P
         del M
+    out[out < 0] = 256.0 * out[out > 0].min()  # an untimed form: 2^8 times the best
     feat = b.cmrs_features(rp, ci).cpu().numpy()
     return feat, out
 
@@ -97,8 +115,10 @@ def build_corpus(specs, device="cuda", reps=5, workers=None, log=None):
 
 
 # ----------------------------------------------------------------------------- network
-def targets_from_times(times):
-    return np.log2(times / times.min(axis=1, keepdims=True)).astype(np.float32)
+def targets_from_times(times, cap=8.0):
+    """log2(t_c / t_best), capped (a form that was not timed counts as 2^cap
+    times the best)."""
+    return np.minimum(np.log2(times / times.min(axis=1, keepdims=True)), cap).astype(np.float32)
 
 
 def init_params(seed=0, nin=b.NFEAT, nh=NH, nout=NCHOICE):
@@ -119,6 +139,8 @@ def normalization(features):
 
 def train(features, times, idx, steps=3000, batch=256, lr=2e-3, seed=0, device="cuda", log=None):
     """Trains on rows `idx` with the library's forward/backward/Adam kernels."""
+    if times.shape[1] != NCHOICE or features.shape[1] != b.NFEAT:
+        raise ValueError("timings must have %d choices and features %d columns" % (NCHOICE, b.NFEAT))
     mean, scale = normalization(features[idx])
     X = torch.from_numpy(((features[idx] - mean) * scale).astype(np.float32)).to(device)
     T = torch.from_numpy(targets_from_times(times[idx])).to(device)

@@ -26,10 +26,16 @@ def corpus():
     return d["features"], d["times"]
 
 
+def choice_tuple(b, c):
+    if c >= 18:
+        return b.SEL_PADDED[c - 18][0], b.CMRS_VARIANT_PADDED, b.SEL_PADDED[c - 18][1]
+    return b.SEL_HEIGHTS[c // 3], c % 3, 0
+
+
 def test_retrained_network_regret_on_held_out(corpus):
     from paper_1203_2946_gb300 import selector
     feats, times = corpus
-    assert feats.shape == (2000, 24) and times.shape == (2000, 18)
+    assert feats.shape == (2000, 24) and times.shape == (2000, 21)
     tr, te = selector.split(len(times), 500, seed=0)
     model = selector.train(feats, times, tr, steps=4000)
     net = selector.regret(times[te], selector.predict(model, feats[te]))
@@ -51,7 +57,7 @@ def test_committed_model_through_select_strip(corpus):
     # picks a valid choice and agrees with the host-side prediction
     a = inputs.banded_random(50000, 700, 10, 60, seed=12)
     rp, ci = torch.from_numpy(a.row_ptr).cuda(), torch.from_numpy(a.col_ind).cuda()
-    h, v = b.cmrs_select_strip(rp, ci, a.cols, model)
+    h, v, m = b.cmrs_select_strip(rp, ci, a.cols, model)
     f = b.cmrs_features(rp, ci).cpu().numpy()[None, :]
     c = int(selector.predict(model, f)[0])
-    assert (h, v) == (b.SEL_HEIGHTS[c // 3], c % 3)
+    assert (h, v, m) == choice_tuple(b, c)

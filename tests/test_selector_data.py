@@ -19,7 +19,7 @@ def _split(n, held_out=500, seed=0):
 def test_corpus_shapes_and_report():
     d = np.load(os.path.join(DATA, "selector_corpus.npz"))
     f, t = d["features"], d["times"]
-    assert f.shape == (2000, 24) and t.shape == (2000, 18)
+    assert f.shape == (2000, 24) and t.shape == (2000, 21)
     assert np.isfinite(f).all() and (t > 0).all()
     specs = json.loads(str(d["specs"]))
     assert len(specs) == 2000 and {s["family"] for s in specs} >= {"stencil2d", "stencil3d", "banded", "blockdiag",
@@ -32,7 +32,7 @@ def test_corpus_shapes_and_report():
 def test_committed_model_regret_with_oracle_forward():
     d = np.load(os.path.join(DATA, "selector_corpus.npz"))
     m = np.load(os.path.join(DATA, "selector_model.npz"))
-    nin, nh, nout = 24, int(m["nh"]), 18
+    nin, nh, nout = 24, int(m["nh"]), 21
     p = m["params"].astype(np.float64)
     sizes = [nh * nin, nh, nh * nh, nh, nout * nh, nout]
     parts = np.split(p, np.cumsum(sizes)[:-1])
