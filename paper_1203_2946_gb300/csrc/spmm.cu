@@ -4,9 +4,14 @@
 // right-hand sides at once, so that each gathered row of X (k contiguous
 // values) is shared by k accumulators.
 //
-// Thread mapping: a group of G = min(32, next_pow2(k)) lanes owns one row,
-// lane g accumulating column c0 + g of Y; columns beyond 32 are done in
-// further passes over the row.  Row bounds inside a strip come from binary
+// Thread mapping: a group of G lanes owns one row.  When k is a multiple of 4
+// and X, Y are 16-byte aligned, lane g accumulates the four columns
+// 4 (c0 + g) .. 4 (c0 + g) + 3 from one 16-byte gather of X (G =
+// min(32, next_pow2(k / 4))): a k = 32 row takes 8 lanes and a warp works
+// four rows at once.  Otherwise lane g accumulates column c0 + g (G =
+// min(32, next_pow2(k))).  Columns beyond the group are done in further
+// passes over the row; each column's sum is one FMA chain in entry order
+// either way.  Row bounds inside a strip come from binary
 // searches on RowInStrip (unsorted strips).  A warp takes 32 / G rows at a
 // time.  Work units (matrix, row range) are fetched by warps from a device
 // queue (one atomic per unit), which balances uneven matrices.
@@ -23,9 +28,13 @@ namespace {
 
 constexpr int kSpmmThreads = 256;
 constexpr int kSpmmCH = 2;  // entries whose gathers are in flight together (8 raised registers to 64 and was slower)
+#ifndef CMRS_SPMM_CH4
+#define CMRS_SPMM_CH4 2  // 16-byte gathers in flight per lane (measured 6.45 ms per batch; 1: 6.72, 3: 7.06, 4: 7.07, 8: 7.73)
+#endif
+constexpr int kSpmmCH4 = CMRS_SPMM_CH4;  // the same for the 16-byte gathers
 
 struct Desc {
-  int32_t rows, height, bits, k;
+  int32_t rows, height, bits, k, vec, pad;
   const int32_t *sp;
   const uint32_t *packed;
   const float *val;
@@ -51,11 +60,80 @@ __device__ __forceinline__ int lb_ris_g(const uint32_t *__restrict__ cp, int lo,
   return lo;
 }
 
+// Lanes that share one row: 16-byte columns when d.vec, else single ones.
+__host__ __device__ __forceinline__ int spmm_lanes(int k, int vec) {
+  const int c = vec ? k / 4 : k;
+  int G = 1;
+  while (G < c && G < 32) G <<= 1;
+  return G;
+}
+
+// Row bounds inside the strip (binary searches on RowInStrip).
+__device__ __forceinline__ void spmm_bounds(const Desc &d, int row, int &k0, int &k1) {
+  const uint32_t mask = (1u << d.bits) - 1;
+  const int s = row / d.height;
+  const uint32_t r = (uint32_t)(row - s * d.height);
+  const int sa = __ldg(d.sp + s), sb = __ldg(d.sp + s + 1);
+  k0 = sa;
+  k1 = sb;
+  if (d.height > 1) {
+    k0 = lb_ris_g(d.packed, sa, sb, r, mask);
+    k1 = lb_ris_g(d.packed, k0, sb, r + 1, mask);
+  }
+}
+
+// Rows [row0, row1) of matrix d, four columns per lane (d.vec).
+__device__ __forceinline__ void spmm_rows4(const Desc &d, int row0, int row1, int lane) {
+  const int kv = d.k >> 2;
+  const int G = spmm_lanes(d.k, 1);
+  const int per = 32 / G;
+  const int g = lane & (G - 1);
+  const int sub = lane / G;
+  const float4 *X4 = reinterpret_cast<const float4 *>(d.X);
+  float4 *Y4 = reinterpret_cast<float4 *>(d.Y);
+  for (int rb = row0; rb < row1; rb += per) {
+    const int row = rb + sub;
+    const bool active = row < row1;
+    int k0 = 0, k1 = 0;
+    if (active) spmm_bounds(d, row, k0, k1);
+    for (int c0 = 0; c0 < kv; c0 += G) {
+      const int col = c0 + g;
+      if (active && col < kv) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = k0; j < k1; j += kSpmmCH4) {
+          float4 xv[kSpmmCH4];
+          float vv[kSpmmCH4];
+#pragma unroll
+          for (int u = 0; u < kSpmmCH4; ++u) {
+            if (j + u < k1) {
+              const uint32_t p = __ldg(d.packed + j + u);
+              vv[u] = __ldg(d.val + j + u);
+              xv[u] = __ldg(X4 + (size_t)(p >> d.bits) * kv + col);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kSpmmCH4; ++u)
+            if (j + u < k1) {
+              acc.x = fmaf(vv[u], xv[u].x, acc.x);
+              acc.y = fmaf(vv[u], xv[u].y, acc.y);
+              acc.z = fmaf(vv[u], xv[u].z, acc.z);
+              acc.w = fmaf(vv[u], xv[u].w, acc.w);
+            }
+        }
+        Y4[(size_t)row * kv + col] = acc;
+      }
+    }
+  }
+}
+
 // Rows [row0, row1) of matrix d, processed by one warp.
 __device__ __forceinline__ void spmm_rows(const Desc &d, int row0, int row1, int lane) {
+  if (d.vec) {
+    spmm_rows4(d, row0, row1, lane);
+    return;
+  }
   const int k = d.k;
-  int G = 1;
-  while (G < k && G < 32) G <<= 1;
+  const int G = spmm_lanes(k, 0);
   const int per = 32 / G;
   const int g = lane & (G - 1);
   const int sub = lane / G;
@@ -148,15 +226,15 @@ Desc make_desc(const cmrs_matrix *A, int k, const float *X, float *Y) {
   d.val = reinterpret_cast<const float *>(A->val);
   d.X = X;
   d.Y = Y;
+  d.vec = (k % 4 == 0) && !((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15);
+  d.pad = 0;
   return d;
 }
 
-int rows_per_unit(const cmrs_matrix *A, int k, int work_target) {
+int rows_per_unit(const cmrs_matrix *A, int k, int vec, int work_target) {
   // work of a row ~ (nnz/rows) * k entry-columns; keep units near work_target
   const double mu = A->rows > 0 ? (double)A->nnz / A->rows : 1.0;
-  int G = 1;
-  while (G < k && G < 32) G <<= 1;
-  const int per = 32 / G;
+  const int per = 32 / spmm_lanes(k, vec);
   double r = work_target / std::max(1.0, mu * k);
   int ri = (int)std::max<double>(per, std::min<double>(r, 1 << 20));
   ri = (ri + per - 1) / per * per;
@@ -188,12 +266,11 @@ extern "C" int cmrs_spmm(const cmrs_matrix *A, int k, const float *X, float *Y, 
     CMRS_CUDA_TRY(cudaMemsetAsync(Y, 0, (size_t)A->rows * k * sizeof(float), st));
     return CMRS_OK;
   }
-  int G = 1;
-  while (G < k && G < 32) G <<= 1;
-  const int rpw = 32 / G;
+  const Desc d = make_desc(A, k, X, Y);
+  const int rpw = 32 / spmm_lanes(k, d.vec);
   const long long warps = ceil_div(A->rows, rpw);
   const int grid = (int)ceil_div(warps * 32, kSpmmThreads);
-  k_spmm_one<<<grid, kSpmmThreads, 0, st>>>(make_desc(A, k, X, Y), rpw);
+  k_spmm_one<<<grid, kSpmmThreads, 0, st>>>(d, rpw);
   CMRS_LAUNCH_CHECK();
   return CMRS_OK;
 }
@@ -202,7 +279,7 @@ static int build_units(int batch, const cmrs_matrix *const *A, const int32_t *k,
                        std::vector<Unit> &units) {
   units.clear();
   for (int b = 0; b < batch; ++b) {
-    const int rpu = rows_per_unit(A[b], k[b], work_target);
+    const int rpu = rows_per_unit(A[b], k[b], k[b] % 4 == 0, work_target);
     for (int r0 = 0; r0 < A[b]->rows; r0 += rpu) {
       Unit u;
       u.mat = b;
