@@ -344,3 +344,29 @@ def test_auto_variant(b, case):
     y_auto = b.cmrs_spmv(M, xs, variant=b.CMRS_VARIANT_AUTO)
     assert torch.equal(y_auto, b.cmrs_spmv(M, xs, variant=want))
     check_spmv(b, M, a, x, b.CMRS_VARIANT_AUTO, 0)
+
+
+def test_largest_column_index(b):
+    """Columns up to 2^27 - 1 at height 32 (5 RowInStrip bits leave 27 column
+    bits in the packed word): conversions bit-exact, products within the bar."""
+    cols = 1 << 27
+    rng = np.random.default_rng(31)
+    L = rng.integers(0, 24, 5000)
+    L[0] = 3
+    a = inputs.from_lengths(L, cols, seed=32)
+    a.col_ind[0:3] = [0, cols // 2, cols - 1]  # row 0: first, middle and last column
+    x = inputs.uniform_vector(cols, 33)
+    xs = torch.from_numpy(x).cuda()
+    yref, absy = orc.csr_spmv(a.row_ptr, a.col_ind, a.val, x)
+    for sorted_ in (False, True):
+        M = check_conversion(b, a, 32, sorted_)
+        for var in (VARIANTS if not sorted_ else [b.CMRS_VARIANT_STRIP]):
+            y = b.cmrs_spmv(M, xs, variant=var).cpu().numpy()
+            assert np.all(np.abs(y - yref) <= 1e-12 * absy), var
+    P = b.cmrs_pad(convert(b, a, 32), 1)
+    assert int(P.col_packed.cpu().numpy()[:P.nnz].view(np.uint32).max() >> 5) == cols - 1
+    y = b.cmrs_spmv(P, xs).cpu().numpy()
+    assert np.all(np.abs(y - yref) <= 1e-12 * absy)
+    with pytest.raises(b.CmrsError):  # one column more does not fit
+        rp, ci = torch.from_numpy(a.row_ptr).cuda(), torch.from_numpy(a.col_ind).cuda()
+        b.cmrs_from_csr(rp, ci, torch.from_numpy(a.val).cuda(), cols + 1, 32)
