@@ -22,6 +22,15 @@ namespace {
 #endif
 constexpr int kRowThreads = CMRS_ROW_ROWS;    // ROW: rows per block
 constexpr int kRowCap = 32 * CMRS_ROW_ROWS;   // ROW: entries per shared-memory stage
+// Resident CTAs per SM asked of the register allocator (shared memory allows
+// about 5): FP64 at 4 keeps 128 registers, the FP32-accumulated forms at 5
+// keep 96, both without spills.
+#ifndef CMRS_MERGE_MINB_F64
+#define CMRS_MERGE_MINB_F64 4
+#endif
+#ifndef CMRS_MERGE_MINB_F32
+#define CMRS_MERGE_MINB_F32 5
+#endif
 constexpr int kMergeThreads = 128;
 constexpr int kMergeE = 15;  // MERGE: entries per thread; odd, so that a warp's shared loads hit 32 banks
 constexpr int kMergeTile = kMergeThreads * kMergeE;
@@ -515,7 +524,8 @@ __global__ void k_tile_map(int strips, const int32_t *__restrict__ sp, int ntile
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kMergeThreads) k_spmv_merge(int rows, int height, int bits, int strips, int nnz,
+__global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MINB_F64 : CMRS_MERGE_MINB_F32)
+    k_spmv_merge(int rows, int height, int bits, int strips, int nnz,
                                                               const int32_t *__restrict__ sp,
                                                               const uint32_t *__restrict__ packed,
                                                               const typename Form<DT>::Stored *__restrict__ hi,
