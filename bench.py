@@ -253,16 +253,24 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU leg
+def kernel_section_sha1(begin, end):
+    """sha1 of the source text of one kernel section of spmv.cu (from the line
+    holding `begin` up to the line holding `end`)."""
+    src = open(os.path.join(ROOT, "paper_1203_2946_gb300", "csrc", "spmv.cu")).read()
+    a = src.index(begin)
+    b = src.index(end, a + len(begin))
+    return hashlib.sha1(src[a:b].encode()).hexdigest()
+
+
 def traffic_record(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, valid only while
-    the kernel source is unchanged."""
+    the kernel's source section is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)[kernel][workload]
-        src = os.path.join(ROOT, "paper_1203_2946_gb300", "csrc", "spmv.cu")
-        h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        return rec["bytes_per_launch"] if rec.get("spmv_cu_sha1") == h else None
+        h = kernel_section_sha1(*rec["section"])
+        return rec["bytes_per_launch"] if rec.get("section_sha1") == h else None
     except Exception:
         return None
 
