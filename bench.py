@@ -51,8 +51,8 @@ def args_parse():
     p.add_argument("--slots", type=int, default=None, help="padded variant: slots per row per warp pass (M of "
                    "Section 6.6; 1, 2, 4 or 8; default 1, irregular 2)")
     p.add_argument("--variant", default=None, choices=["row", "strip", "merge", "auto", "padded"],
-                   help="SpMV kernel variant (default: padded for the 27-point headline; power-law merge; "
-                        "p7 and dense4 auto; else row)")
+                   help="SpMV kernel variant (default: padded for the 27-point headline and p7; power-law "
+                        "merge; dense4 auto; else row)")
     p.add_argument("--workload", default="stencil27",
                    choices=["stencil27", "powerlaw", "batched", "laplacian", "p7", "dense4", "irregular"],
                    help="stencil27 is the headline; the others print the same JSON schema for their workload")
@@ -565,7 +565,7 @@ def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
 def main():
     args = args_parse()
     if args.variant is None:
-        args.variant = {"stencil27": "padded", "powerlaw": "merge", "p7": "auto", "dense4": "auto"}.get(
+        args.variant = {"stencil27": "padded", "powerlaw": "merge", "p7": "padded", "dense4": "auto"}.get(
             args.workload, "row")
     if args.height is None:
         args.height = 32 if args.workload in ("powerlaw", "p7") or args.variant == "padded" else 4
@@ -628,7 +628,7 @@ def run_secondary(args):
         h, v = args.height, dict(b.VARIANTS, auto=b.CMRS_VARIANT_AUTO, padded=b.CMRS_VARIANT_PADDED)[args.variant]
         rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
         va = torch.from_numpy(np.ascontiguousarray(a.val)).to(dev)
-        M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=dt)
+        M = M_plain = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=dt)
         if args.variant == "padded":
             M = b.cmrs_pad(M, args.slots)
         ran = b.cmrs_spmv_variant(M, v)
@@ -653,15 +653,12 @@ def run_secondary(args):
         if not args.no_cpu:
             extra["cpu_baseline"] = cpu_oracle_rate(inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind,
                                                                a.val.astype(np.float64)), x.astype(np.float64), S)
+        extra["stored_items_per_nnz"] = M.nnz / max(a.nnz, 1)
         if args.workload in ("p7", "dense4"):
             var = {}
-            for vn, vv in b.VARIANTS.items():
-                try:
-                    b.cmrs_spmv_variant(M, vv)
-                except b.CmrsError:
-                    continue  # not defined on this matrix (padded strips)
-                vws = M.spmv_workspace(vv)
-                g = lambda: b.cmrs_spmv(M, xd, yd, vv, vws)  # noqa: E731
+            for vn, vv in b.VARIANTS.items():  # plain CMRS at the same height
+                vws = M_plain.spmv_workspace(vv)
+                g = lambda: b.cmrs_spmv(M_plain, xd, yd, vv, vws)  # noqa: E731
                 for _ in range(2):
                     g()
                 vms = statistics.mean(time_steps(g, 20, flush, stream))
