@@ -31,7 +31,7 @@ from . import inputs
 HEIGHTS = b.SEL_HEIGHTS
 NCHOICE = b.SEL_CHOICES
 NH = 64
-FORMAT_VERSION = 1
+FORMAT_VERSION = 2  # 2: 21 choices (plain CMRS and the three padded forms)
 
 
 PADDED = b.SEL_PADDED
@@ -198,5 +198,9 @@ def load_model(path, device="cuda"):
     d = np.load(path)
     if int(d["version"]) != FORMAT_VERSION:
         raise ValueError("selector model format %d, expected %d" % (int(d["version"]), FORMAT_VERSION))
+    nh = int(d["nh"])
+    want = nh * b.NFEAT + nh + nh * nh + nh + NCHOICE * nh + NCHOICE
+    if d["params"].size != want or d["mean"].size != b.NFEAT or d["scale"].size != b.NFEAT:
+        raise ValueError("selector model does not match %d features and %d choices" % (b.NFEAT, NCHOICE))
     return {"params": torch.from_numpy(d["params"]).to(device), "mean": torch.from_numpy(d["mean"]).to(device),
             "scale": torch.from_numpy(d["scale"]).to(device), "nh": int(d["nh"])}

@@ -5,6 +5,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 import oracle
 
@@ -45,3 +46,19 @@ def test_committed_model_regret_with_oracle_forward():
     choice = O[te].argmin(axis=1)
     r = times[te, choice] / times[te].min(axis=1)
     assert np.exp(np.mean(np.log(r))) <= 1.10
+
+
+def test_model_file_checks(tmp_path):
+    """load_model refuses an older format or a network of another width."""
+    from paper_1203_2946_gb300 import selector
+    m = dict(np.load(os.path.join(DATA, "selector_model.npz")))
+    ok = selector.load_model(os.path.join(DATA, "selector_model.npz"), device="cpu")
+    assert ok["params"].numel() == m["params"].size
+    bad = dict(m, params=m["params"][:-3 * 65])  # 18 outputs
+    np.savez(tmp_path / "narrow.npz", **bad)
+    with pytest.raises(ValueError):
+        selector.load_model(str(tmp_path / "narrow.npz"), device="cpu")
+    old = dict(m, version=np.array(1))
+    np.savez(tmp_path / "old.npz", **old)
+    with pytest.raises(ValueError):
+        selector.load_model(str(tmp_path / "old.npz"), device="cpu")
