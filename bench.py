@@ -49,10 +49,10 @@ def args_parse():
     p.add_argument("--height", type=int, default=None,
                    help="strip height (default: 32 for the 27-point headline, power-law and p7; else 4)")
     p.add_argument("--slots", type=int, default=None, help="padded variant: slots per row per warp pass (M of "
-                   "Section 6.6; 1, 2, 4 or 8; default 1, irregular 2)")
+                   "Section 6.6; 1, 2, 4 or 8; default 1, irregular 2, dense4 8)")
     p.add_argument("--variant", default=None, choices=["row", "strip", "merge", "auto", "padded"],
-                   help="SpMV kernel variant (default: padded for the 27-point headline and p7; power-law "
-                        "merge; dense4 auto; else row)")
+                   help="SpMV kernel variant (default: padded for the 27-point headline, p7 and dense4; "
+                        "power-law merge; else row)")
     p.add_argument("--workload", default="stencil27",
                    choices=["stencil27", "powerlaw", "batched", "laplacian", "p7", "dense4", "irregular"],
                    help="stencil27 is the headline; the others print the same JSON schema for their workload")
@@ -572,12 +572,13 @@ def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
 def main():
     args = args_parse()
     if args.variant is None:
-        args.variant = {"stencil27": "padded", "powerlaw": "merge", "p7": "padded", "dense4": "auto"}.get(
+        args.variant = {"stencil27": "padded", "powerlaw": "merge", "p7": "padded", "dense4": "padded"}.get(
             args.workload, "row")
     if args.height is None:
-        args.height = 32 if args.workload in ("powerlaw", "p7") or args.variant == "padded" else 4
+        args.height = 4 if args.workload == "dense4" else (
+            32 if args.workload in ("powerlaw", "p7") or args.variant == "padded" else 4)
     if args.slots is None:
-        args.slots = 2 if args.workload == "irregular" else 1
+        args.slots = {"irregular": 2, "dense4": 8}.get(args.workload, 1)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stencil27":
