@@ -3,7 +3,7 @@
 // 6.2 picks the strip height by brute force over all heights and Section 6.7
 // measures how much per-matrix tuning gains; here a network trained on this
 // library's own timings predicts the choice, with the brute-force sweep as
-// fallback and as the judge of its regret.
+// fallback and as the yardstick of its regret.
 #include <algorithm>
 #include <cmath>
 #include <vector>
