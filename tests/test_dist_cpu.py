@@ -52,3 +52,16 @@ def test_beta_plus_matches_eq_6_1():
     import oracle
     for nnz, rows, strips, sv in [(55_742_968, 2_097_152, 524_288, 8), (20_224, 4_096, 1_024, 8)]:
         assert bench.beta_plus(nnz, rows, strips, sv) == oracle.beta(nnz, rows, strips, sv)[1]
+
+
+def test_beta_minus_and_eta_match_eq_6_1():
+    """The bench's beta- (input vector not cached) and eta+- follow Eq. 6.1 as the oracle states it."""
+    import bench
+    import oracle
+    for nnz, rows, strips, sv in ((55742968, 2097152, 65536, 8), (21503218, 4194304, 131072, 4), (20224, 4096, 1024, 8)):
+        bm, bp = oracle.beta(nnz, rows, strips, sv)
+        assert bench.beta_minus(nnz, rows, strips, sv) == bm
+        e = bench.eta(nnz, rows, strips, sv, 0.1, 1000.0)  # 0.1 ms, B = 1000 GB/s
+        assert abs(e["eta_plus"] - bp / 1e-4 / 1e9 / 1000.0) < 1e-12
+        assert abs(e["eta_minus"] - bm / 1e-4 / 1e9 / 1000.0) < 1e-12
+        assert abs(e["beta_minus_gbs"] - bm / 1e-4 / 1e9) < 1e-9
