@@ -137,9 +137,12 @@ def _check(rc, where):
 
 
 def workspace(nbytes, device="cuda"):
-    """A zero-filled, 256-byte aligned device workspace (torch allocations are)."""
-    t = torch.zeros(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    """A 256-byte aligned device workspace (torch allocations are) whose first
+    256 bytes -- the status block every entry point keeps there -- start at
+    zero; the library initialises whatever else it reads."""
+    t = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
     assert t.data_ptr() % 256 == 0
+    t[:256].zero_()
     return t
 
 

@@ -8,6 +8,8 @@ namespace cmrs {
 namespace {
 
 constexpr int kSortShortCap = 1024;  // strips up to this length: warp bitonic sort in shared memory
+constexpr int kSortMergeRows = 8;    // heights up to this: rows already in column order are merged
+constexpr int kSortBatch = 4;        // independent loads each lane issues before using them
 constexpr int kSortWarps = 4;
 constexpr int kRadixThreads = 128;   // CTA radix sort for longer strips
 constexpr int kRadixWarps = kRadixThreads / 32;
@@ -115,11 +117,18 @@ __global__ void k_pack(int rows, int cols, int nnz, int height, int bits, const 
 
 // ---------------------------------------------------------------- in-strip sort
 // Section 4, fourth optimisation: each strip's entries ordered by column,
-// ties kept in CRS order.  Short strips: one warp sorts unique 64-bit keys
-// (column << 32 | position in strip) with a bitonic network in shared memory,
-// which makes the order stable.  The payload is then gathered by position.
+// ties kept in CRS order.  Short strips, one warp each.  When the strip's
+// rows are each already in column order (the usual CRS) and the height is at
+// most kSortMergeRows, the stable order is a merge of the rows: an entry's
+// place is its index in its row plus, for every other row, the number of
+// that row's entries before it (earlier rows: columns <= its column; later
+// rows: columns <), found by binary search.  Otherwise the warp sorts unique
+// 64-bit keys (column << 32 | position in strip) with a bitonic network in
+// shared memory, which makes the order stable, and gathers the payload by
+// position.
 template <int DT>
-__global__ void __launch_bounds__(kSortWarps * 32) k_sort_short(int strips, int bits, const int32_t *__restrict__ sp,
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_short(int strips, int height, int bits,
+                                                                 const int32_t *__restrict__ sp,
                                                                  const uint32_t *__restrict__ pin,
                                                                  const typename Encode<DT>::Out *__restrict__ hin,
                                                                  const typename Encode<DT>::Out *__restrict__ lin,
@@ -130,13 +139,118 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_short(int strips, int 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t *keys = keys_all[w];
   const int nw = gridDim.x * kSortWarps;
-  for (int s = blockIdx.x * kSortWarps + w; s < strips; s += nw) {
-    const int32_t a = sp[s], len = sp[s + 1] - a;
+  typedef typename Encode<DT>::Out Out;
+  const uint32_t mask = (1u << bits) - 1;
+  int s = blockIdx.x * kSortWarps + w;
+  int32_t na = s < strips ? sp[s] : 0, nb = s < strips ? sp[s + 1] : 0;
+  for (; s < strips; s += nw) {
+    const int32_t a = na, len = nb - na;
+    if (s + nw < strips) {  // the next strip's bounds, loaded ahead
+      na = sp[s + nw];
+      nb = sp[s + nw + 1];
+    }
     if (len > kSortShortCap || len <= 0) continue;
+    if (height <= kSortMergeRows) {
+      // the strip's packed words, staged in this warp's shared buffer for the searches
+      uint32_t *w32 = reinterpret_cast<uint32_t *>(keys);
+      for (int i0 = 0; i0 < len; i0 += 32 * kSortBatch) {
+        uint32_t v[kSortBatch];
+#pragma unroll
+        for (int u = 0; u < kSortBatch; ++u) {
+          const int i = i0 + 32 * u + lane;
+          v[u] = i < len ? pin[a + i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortBatch; ++u) {
+          const int i = i0 + 32 * u + lane;
+          if (i < len) w32[i] = v[u];
+        }
+      }
+      __syncwarp();
+      // first entry of row `lane` (RowInStrip is non-decreasing in an unsorted strip)
+      int start = 0;
+      if (lane > 0 && lane < height) {
+        int lo = 0, hi = len;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if ((w32[mid] & mask) < (uint32_t)lane) lo = mid + 1;
+          else hi = mid;
+        }
+        start = lo;
+      }
+      int end = __shfl_down_sync(0xffffffffu, start, 1);
+      if (lane == height - 1) end = len;
+      bool unordered = false;
+      for (int i = lane + 1; i < len; i += 32) {
+        const uint32_t p = w32[i], q = w32[i - 1];
+        if ((p & mask) == (q & mask) && (p >> bits) < (q >> bits)) unordered = true;
+      }
+      int rs[kSortMergeRows], re[kSortMergeRows];
+#pragma unroll
+      for (int r = 0; r < kSortMergeRows; ++r) {
+        rs[r] = __shfl_sync(0xffffffffu, start, r);
+        re[r] = __shfl_sync(0xffffffffu, end, r);
+      }
+      if (!__any_sync(0xffffffffu, unordered)) {
+        for (int i0 = 0; i0 < len; i0 += 32 * kSortBatch) {
+          Out hv[kSortBatch], lv[kSortBatch];
+#pragma unroll
+          for (int u = 0; u < kSortBatch; ++u) {
+            const int i = i0 + 32 * u + lane;
+            if (i < len) {
+              hv[u] = hin[a + i];
+              if (DT == CMRS_BF16X2) lv[u] = lin[a + i];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kSortBatch; ++u) {
+            const int i = i0 + 32 * u + lane;
+            if (i >= len) continue;
+            const uint32_t p = w32[i];
+            const int r = (int)(p & mask);
+            const uint32_t c = p >> bits;
+            int rank = 0;
+#pragma unroll
+            for (int q = 0; q < kSortMergeRows; ++q) {
+              if (q >= height) break;
+              if (q == r) {
+                rank += i - rs[q];
+              } else {
+                int lo = rs[q], hi = re[q];
+                while (lo < hi) {
+                  const int mid = (lo + hi) >> 1;
+                  const uint32_t cm = w32[mid] >> bits;
+                  if (q < r ? cm <= c : cm < c) lo = mid + 1;
+                  else hi = mid;
+                }
+                rank += lo - rs[q];
+              }
+            }
+            pout[a + rank] = p;
+            hout[a + rank] = hv[u];
+            if (DT == CMRS_BF16X2) lout[a + rank] = lv[u];
+          }
+        }
+        __syncwarp();  // the buffer is reused by the next strip
+        continue;
+      }
+      __syncwarp();  // the bitonic path below overwrites the staged words
+    }
     int n2 = 1;
     while (n2 < len) n2 <<= 1;
-    for (int i = lane; i < n2; i += 32)
-      keys[i] = i < len ? ((uint64_t)(pin[a + i] >> bits) << 32) | (uint32_t)i : ~0ull;
+    for (int i0 = 0; i0 < n2; i0 += 32 * kSortBatch) {
+      uint32_t v[kSortBatch];
+#pragma unroll
+      for (int u = 0; u < kSortBatch; ++u) {
+        const int i = i0 + 32 * u + lane;
+        v[u] = i < len ? pin[a + i] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kSortBatch; ++u) {
+        const int i = i0 + 32 * u + lane;
+        if (i < n2) keys[i] = i < len ? ((uint64_t)(v[u] >> bits) << 32) | (uint32_t)i : ~0ull;
+      }
+    }
     __syncwarp();
     for (int k = 2; k <= n2; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
@@ -154,11 +268,28 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_short(int strips, int 
         __syncwarp();
       }
     }
-    for (int i = lane; i < len; i += 32) {
-      int32_t src = a + (int32_t)(keys[i] & 0xffffffffu);
-      pout[a + i] = pin[src];
-      hout[a + i] = hin[src];
-      if (DT == CMRS_BF16X2) lout[a + i] = lin[src];
+    for (int i0 = 0; i0 < len; i0 += 32 * kSortBatch) {
+      uint32_t pv[kSortBatch];
+      Out hv[kSortBatch], lv[kSortBatch];
+#pragma unroll
+      for (int u = 0; u < kSortBatch; ++u) {
+        const int i = i0 + 32 * u + lane;
+        if (i < len) {
+          const int32_t src = a + (int32_t)(keys[i] & 0xffffffffu);
+          pv[u] = pin[src];
+          hv[u] = hin[src];
+          if (DT == CMRS_BF16X2) lv[u] = lin[src];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kSortBatch; ++u) {
+        const int i = i0 + 32 * u + lane;
+        if (i < len) {
+          pout[a + i] = pv[u];
+          hout[a + i] = hv[u];
+          if (DT == CMRS_BF16X2) lout[a + i] = lv[u];
+        }
+      }
     }
     __syncwarp();
   }
@@ -179,8 +310,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_long(int strips, int bit
                                                              typename Encode<DT>::Out *__restrict__ hout,
                                                              typename Encode<DT>::Out *__restrict__ lout,
                                                              uint32_t *__restrict__ keyA, uint32_t *__restrict__ posA,
-                                                             uint32_t *__restrict__ keyB, uint32_t *__restrict__ posB) {
+                                                             uint32_t *__restrict__ keyB, uint32_t *__restrict__ posB,
+                                                             const StatusBlock *__restrict__ stb) {
   __shared__ int hist[256];
+  if (stb->max_strip <= kSortShortCap) return;  // no long strip: nothing to do
   __shared__ int base[256];
   __shared__ int ccount[256];
   __shared__ int wcnt[kRadixWarps][257];
@@ -380,8 +513,10 @@ int from_csr_impl(int rows, int cols, int nnz, int height, int bits, uint32_t fl
   if (sorted && nnz > 0 && strips > 0) {
     Out *oh = reinterpret_cast<Out *>(val_out);
     Out *ol = DT == CMRS_BF16X2 ? oh + cmrs_pad8(nnz) : nullptr;
-    int gs = (int)std::min<int64_t>(ceil_div(strips, kSortWarps), (int64_t)sms * 8);
-    k_sort_short<DT><<<gs, kSortWarps * 32, 0, st>>>(strips, bits, strip_ptr, pk, vh, vl, packed, oh, ol);
+    int per_sm = 0;  // one resident wave: every warp walks the same number of strips
+    CMRS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_short<DT>, kSortWarps * 32, 0));
+    int gs = (int)std::min<int64_t>(ceil_div(strips, kSortWarps), (int64_t)sms * std::max(1, per_sm));
+    k_sort_short<DT><<<gs, kSortWarps * 32, 0, st>>>(strips, height, bits, strip_ptr, pk, vh, vl, packed, oh, ol);
     CMRS_LAUNCH_CHECK();
     int col_bits = 1;
     while (col_bits < 31 && ((int64_t)1 << col_bits) < (int64_t)cols) ++col_bits;
@@ -390,7 +525,7 @@ int from_csr_impl(int rows, int cols, int nnz, int height, int bits, uint32_t fl
                                                   reinterpret_cast<uint32_t *>(ws + L.keyA),
                                                   reinterpret_cast<uint32_t *>(ws + L.posA),
                                                   reinterpret_cast<uint32_t *>(ws + L.keyB),
-                                                  reinterpret_cast<uint32_t *>(ws + L.posB));
+                                                  reinterpret_cast<uint32_t *>(ws + L.posB), sb);
     CMRS_LAUNCH_CHECK();
   }
   StatusBlock host;

@@ -370,3 +370,22 @@ def test_largest_column_index(b):
     with pytest.raises(b.CmrsError):  # one column more does not fit
         rp, ci = torch.from_numpy(a.row_ptr).cuda(), torch.from_numpy(a.col_ind).cuda()
         b.cmrs_from_csr(rp, ci, torch.from_numpy(a.val).cuda(), cols + 1, 32)
+
+
+@pytest.mark.parametrize("h", [1, 2, 4, 8, 16])
+def test_sorted_conversion_of_unordered_rows(b, h):
+    """In-strip sort when CRS rows are not in column order (some rows shuffled,
+    columns repeated across the rows of a strip): the stable column order of
+    the oracle, bit for bit, whichever path the kernel takes."""
+    rng = np.random.default_rng(40 + h)
+    a = inputs.from_lengths(rng.integers(0, 40, 3000), 64, seed=41)  # 64 columns: many equal columns per strip
+    ci = a.col_ind.copy()
+    for i in rng.choice(a.rows, 700, replace=False):
+        s, e = a.row_ptr[i], a.row_ptr[i + 1]
+        ci[s:e] = rng.permutation(ci[s:e])
+    a = inputs.CSR(a.rows, a.cols, a.row_ptr, ci, a.val)
+    for dtype in (0, 3):
+        check_conversion(b, a, h, True, dtype)
+    # rows all in order: the merge path; the same oracle order
+    a2 = inputs.from_lengths(rng.integers(0, 40, 3000), 64, seed=42)
+    check_conversion(b, a2, h, True, 0)
