@@ -2,11 +2,13 @@
 """CMRS SpMV benchmark on GB300.
 
 Workload (default): 27-point stencil on a 128^3 grid, non-periodic
-(n = 2,097,152 rows, nnz = 55,742,968), FP64 values, x ~ U[-1, 1], CMRS with
-strip height h, SpMV kernel variant ROW.  One step = one y = A x through
-cmrs_spmv.  Inputs are resident in HBM before the timed region; the L2 is
-flushed (256 MiB write) between steps and every step is timed by its own pair
-of CUDA events on the launching stream.
+(n = 2,097,152 rows, nnz = 55,742,968), FP64 values, x ~ U[-1, 1], stored as
+the modified CMRS of Section 6.6 (strip height 32, one slot per row per
+pass), SpMV kernel PADDED.  One step = one y = A x through cmrs_spmv.  Inputs
+are resident in HBM before the timed region; the L2 is flushed between steps
+(256 MiB write, then a 256 MiB read so that the write's dirty lines are not
+written back inside the step) and every step is timed by its own pair of CUDA
+events on the launching stream.
 
 Metric: GB/s = beta_plus / t with beta_plus = (s_v + s_i) nnz + s_i strips +
 2 s_v rows (Eq. 6.1: matrix, x and y moved once), also GFLOP/s = 2 nnz / t and
@@ -331,12 +333,36 @@ def e2e_pipelined(run, xh, xds, yds, yhs, steps, warm=3):
                               lambda s: yhs[s].copy_(yds[s], non_blocking=True), steps, warm)
 
 
+L2_NOTE = ("flushed between steps (256 MiB write, then a 256 MiB read so that the dirty lines the write leaves "
+           "are written back before the step, not inside it), each step timed by its own CUDA events")
+
+
+class L2Flush:
+    """Between timed steps: write a 256 MiB buffer, which evicts every line of
+    the step's operands from the L2 (about 126 MB), then read a second 256 MiB
+    buffer.  A write alone leaves the L2 full of dirty lines that the next
+    kernel pays to write back to HBM (about 5 us for the FP64 headline, 8 us
+    for split BF16); after the read the L2 holds only clean lines of neither
+    the matrix nor x nor y."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        self.r = torch.ones(32 << 20, dtype=torch.int64, device=dev)
+        self.acc = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def __call__(self, i):
+        import torch
+        self.w.fill_(i & 0xFF)
+        torch.sum(self.r, dim=0, keepdim=True, out=self.acc)
+
+
 def time_steps(fn, steps, flush, stream):
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for i in range(steps):
-        flush.fill_(i & 0xFF)
+        flush(i)
         starts[i].record(stream)
         fn()
         ends[i].record(stream)
@@ -368,7 +394,7 @@ def run_ours(args):
     xd = torch.from_numpy(x).to(dev)
     yd = torch.empty(a.rows, dtype=torch.float64, device=dev)
     ws = M.spmv_workspace(variant)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
 
     def step():
         b.cmrs_spmv(M, xd, yd, binding_variant, ws)
@@ -417,7 +443,7 @@ def run_ours(args):
                    "height": h, "variant": args.variant, "bytes_per_step": bp,
                    "slots": args.slots if args.variant == "padded" else None,
                    "stored_items_per_nnz": M.nnz / a.nnz,
-                   "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events",
+                   "l2": L2_NOTE,
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU"},
         "gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
         "gflops_paper": (2 * a.nnz - a.rows) / (per_ms / 1e3) / 1e9,
@@ -609,7 +635,7 @@ def run_secondary(args):
     import oracle
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(None)
     steps = args.steps
@@ -703,7 +729,7 @@ def run_secondary(args):
         line = _line(args, gbs, "GB/s", per_ms, name,
                      {"workload": wl, "height": h, "variant": args.variant,
                       "kernel_variant": ("row", "strip", "merge", "padded")[ran], "bytes_per_step": bp,
-                      "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
+                      "l2": L2_NOTE},
                      {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                       "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": kname},
                      {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(x.nbytes),
@@ -795,7 +821,7 @@ def run_secondary(args):
                               "k in {1,4,8,32}), FP32, CMRS h=%d; one persistent graph-replayed launch" % (len(specs), h),
                   "matrices": len(specs), "rows_total": rows_total, "entry_columns": nnz_total,
                   "bytes_per_step": bp, "schedule": {"work_target": best, **info},
-                  "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
+                  "l2": L2_NOTE},
                  {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                   "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmm_queue"},
                  {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s",
@@ -832,7 +858,7 @@ def run_irregular(args):
     import oracle
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(None)
     a, x = inputs.workload_irregular()
@@ -916,7 +942,7 @@ def run_irregular(args):
                                                    "the row map; " % args.window if args.window else "", args.slots),
                   "height": h, "variant": "padded", "slots": args.slots, "window": args.window,
                   "stored_items_per_nnz": P.nnz / a.nnz, "bytes_per_step": bp,
-                  "l2": "flushed between steps (256 MiB write), each step timed by its own CUDA events"},
+                  "l2": L2_NOTE},
                  {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                   "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmv_padded"},
                  {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(x.nbytes),
