@@ -194,15 +194,19 @@ int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *col_ind_out
  * Same storage form as A (BF16X2: hi then lo at 2 * cmrs_pad8(nnz_padded)
  * bytes).
  *
+ * A must be a valid unsorted CMRS matrix (RowInStrip non-decreasing within
+ * each strip, as cmrs_from_csr writes it).
  * cmrs_pad_layout: writes the padded StripPtr (device, [strips+1], multiples
  * of 32) and the padded item count (host *nnz_padded).  Synchronises
  * `stream` once to read the count.  CMRS_ERR_ARG if the count reaches 2^31,
  * CMRS_ERR_UNSUPPORTED for sorted or padded input, CMRS_ERR_HEIGHT for
- * height < 4.  workspace: >= cmrs_pad_workspace() bytes, 256-byte aligned.
+ * height < 4, CMRS_ERR_CSR_INVALID for a strip whose row bounds it finds out
+ * of order.  workspace: >= cmrs_pad_workspace() bytes, 256-byte aligned.
  * cmrs_pad_fill: writes col_packed_out[nnz_padded] and val_out (device,
  * cmrs_val_bytes(nnz_padded, A->dtype) bytes, 16-byte aligned) and *out (a
  * view of strip_ptr_padded, col_packed_out and val_out with CMRS_PADDED set).
- * Asynchronous.  A padded matrix multiplies x[0] by zero in its zero items:
+ * Asynchronous; it writes no more passes per strip than the layout gave it.
+ * A padded matrix multiplies x[0] by zero in its zero items:
  * x must be finite there.  cmrs_to_csr does not accept padded matrices. */
 int cmrs_pad_workspace(const cmrs_matrix *A, int slots, size_t *bytes);
 int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_ptr_padded, int32_t *nnz_padded,

@@ -11,9 +11,18 @@
 // the remaining C - 1 passes cannot hold), free room then goes to the rows
 // with most items left (ties: lower row) up to min(left, M) each, and room
 // still free becomes zero items, rows 0 upwards, each row topped up to M.
-// Inside a pass the rows appear in ascending order, each one run.  The
-// layout pass runs the plan only to count passes; a scan turns the counts
-// into the padded StripPtr; the fill pass runs the plan again and writes.
+// Inside a pass the rows appear in ascending order, each one run.
+//
+// The plan always ends after exactly C0 = max(ceil(T / 32), ceil(L / M))
+// passes (T the strip's items, L its longest row), the fewest any arrangement
+// can have: with C passes left every row holds at most M C items, so each
+// forced take max(0, left - M (C - 1)) is at most left / C and together they
+// fit in one pass; the pass then takes min(32, sum of min(left, M)) items,
+// which is at least total - 32 (C - 1) because left - min(left, M) <=
+// left (C - 1) / C; so after it both the total and the longest row fit in
+// C - 1 passes.  The layout pass therefore counts C0 per strip from T and L
+// alone; a scan turns the counts into the padded StripPtr; the fill pass runs
+// the plan and writes, never more passes than the layout gave the strip.
 #include <algorithm>
 
 #include "common.cuh"
@@ -36,18 +45,10 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   return incl - v;
 }
 
-// Plans (and with kFill writes) strip s.  Returns its pass count, or -1 if a
-// plan overflowed a pass (cannot happen for valid unsorted strips; kept as a
-// guard so that a corrupt input never writes past its strip).
-template <bool kFill, typename S, bool kSplit>
-__device__ long long pad_strip(int s, int height, int bits, int slots, const int32_t *__restrict__ sp,
-                               const uint32_t *__restrict__ packed, const S *__restrict__ vh,
-                               const S *__restrict__ vl, long long out0, uint32_t *__restrict__ pk_out,
-                               S *__restrict__ vo_h, S *__restrict__ vo_l) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t mask = (1u << bits) - 1;
-  const int sa = sp[s], sb = sp[s + 1];
-  // first item of row `lane` (RowInStrip is non-decreasing in an unsorted strip)
+// First item of row `lane` of strip [sa, sb) (RowInStrip is non-decreasing
+// in an unsorted strip) and its item count; lanes at or past the height get 0.
+__device__ __forceinline__ int row_span(int sa, int sb, int height, uint32_t mask,
+                                        const uint32_t *__restrict__ packed, int lane, int *first) {
   int start = sa;
   if (lane > 0 && lane < height) {
     int lo = sa, hi = sb;
@@ -60,28 +61,52 @@ __device__ long long pad_strip(int s, int height, int bits, int slots, const int
   }
   int end = __shfl_down_sync(kFull, start, 1);
   if (lane == height - 1) end = sb;
-  int left = lane < height ? end - start : 0;
-  int next = start;
+  *first = start;
+  return lane < height ? end - start : 0;
+}
+
+// Runs the plan of strip s and writes its passes from out0 on, at most
+// `limit` of them.  Returns false if the plan does not fit (a pass
+// overflowing, or more passes than `limit`), which a valid unsorted strip
+// never does; the writes stay inside the strip's limit either way.
+template <typename S, bool kSplit>
+__device__ bool pad_strip_fill(int sa, int sb, int height, int bits, int slots, long long limit,
+                               const uint32_t *__restrict__ packed, const S *__restrict__ vh,
+                               const S *__restrict__ vl, long long out0, uint32_t *__restrict__ pk_out,
+                               S *__restrict__ vo_h, S *__restrict__ vo_l) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << bits) - 1;
+  int next;
+  int left = row_span(sa, sb, height, mask, packed, lane, &next);
+  if (left < 0) left = 0;  // a corrupt strip: what is left unwritten is reported below
   long long passes = 0;
   for (;;) {
     const int total = (int)__reduce_add_sync(kFull, (unsigned)left);
     if (total == 0) break;
+    if (passes == limit) return false;
     const int longest = (int)__reduce_max_sync(kFull, (unsigned)left);
     const int C = max((total + 31) / 32, (longest + slots - 1) / slots);
     int take = max(0, left - slots * (C - 1));
     int room = 32 - (int)__reduce_add_sync(kFull, (unsigned)take);
-    if (room < 0) return -1;
+    if (room < 0) return false;
     // free room: rows with most items left first, lower row on ties
     const int want = min(left, slots) - take;
-    const unsigned long long key =
-        want > 0 ? ((unsigned long long)(left - take) << 6) | (unsigned long long)(63 - lane) : 0ull;
-    int before = 0;
-    for (int j = 0; j < 32; ++j) {
-      const unsigned long long kj = __shfl_sync(kFull, key, j);
-      const int wj = __shfl_sync(kFull, want, j);
-      if (kj > key) before += wj;
+    const int wanted = (int)__reduce_add_sync(kFull, (unsigned)max(want, 0));
+    int extra;
+    if (wanted <= room) {
+      extra = max(want, 0);  // every row gets what it wants
+    } else {
+      const unsigned long long key =
+          want > 0 ? ((unsigned long long)(left - take) << 6) | (unsigned long long)(63 - lane) : 0ull;
+      int before = 0;
+      for (unsigned m = __ballot_sync(kFull, want > 0); m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        const unsigned long long kj = __shfl_sync(kFull, key, j);
+        const int wj = __shfl_sync(kFull, want, j);
+        if (kj > key) before += wj;
+      }
+      extra = want > 0 ? max(0, min(want, room - before)) : 0;
     }
-    const int extra = want > 0 ? max(0, min(want, room - before)) : 0;
     take += extra;
     room -= (int)__reduce_add_sync(kFull, (unsigned)extra);
     // zero items: rows 0 upwards, each topped up to `slots`
@@ -89,14 +114,14 @@ __device__ long long pad_strip(int s, int height, int bits, int slots, const int
     const int zero = max(0, min(zcap, room - warp_excl_scan(zcap, lane)));
     const int len = take + zero;
     const int off = warp_excl_scan(len, lane);
-    if (kFill) {
-      const long long base = out0 + passes * 32 + off;
-      for (int j = 0; j < take; ++j) {
+    const long long base = out0 + passes * 32 + off;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {  // slots <= 8 items of a row per pass
+      if (j < take) {
         pk_out[base + j] = packed[next + j];
         vo_h[base + j] = vh[next + j];
         if (kSplit) vo_l[base + j] = vl[next + j];
-      }
-      for (int j = take; j < len; ++j) {
+      } else if (j < len) {
         pk_out[base + j] = (uint32_t)lane;  // column 0, this row
         vo_h[base + j] = S(0);
         if (kSplit) vo_l[base + j] = S(0);
@@ -106,22 +131,70 @@ __device__ long long pad_strip(int s, int height, int bits, int slots, const int
     left -= take;
     ++passes;
   }
-  return passes;
+  return passes == limit;
 }
 
+// Passes of each strip: max(ceil(T / 32), ceil(L / M)), 0 for an empty strip.
 __global__ void __launch_bounds__(kPadWarps * 32) k_pad_count(int strips, int height, int bits, int slots,
                                                              const int32_t *__restrict__ sp,
                                                              const uint32_t *__restrict__ packed,
                                                              int32_t *__restrict__ counts, uint32_t *status) {
   const int nw = gridDim.x * kPadWarps;
+  const int lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << bits) - 1;
   for (int s = blockIdx.x * kPadWarps + (threadIdx.x >> 5); s < strips; s += nw) {
-    const long long c = pad_strip<false, uint32_t, false>(s, height, bits, slots, sp, packed, nullptr, nullptr, 0,
-                                                          nullptr, nullptr, nullptr);
-    if ((threadIdx.x & 31) == 0) {
-      if (c < 0) atomicOr(status, ST_PAD_PLAN);
-      counts[s] = c < 0 ? 0 : (c > 0x7fffffffLL ? 0x7fffffff : (int32_t)c);
+    const int sa = sp[s], sb = sp[s + 1];
+    int first;
+    const int len = row_span(sa, sb, height, mask, packed, lane, &first);
+    const bool bad = __any_sync(kFull, len < 0) || sb < sa;
+    const int longest = (int)__reduce_max_sync(kFull, (unsigned)max(len, 0));
+    if (lane == 0) {
+      if (bad) atomicOr(status, ST_PAD_PLAN);
+      const long long T = bad ? 0 : sb - sa;
+      const long long c = std::max((T + 31) / 32, ((long long)longest + slots - 1) / slots);
+      counts[s] = bad ? 0 : (int32_t)std::min<long long>(c, 0x7fffffffLL);
     }
   }
+}
+
+// M = 1 (so height 32): every row with items left takes exactly one per pass
+// (the forced takes and the free room together never turn a row away), so
+// pass p holds item p of row r at position r, or a zero item of row r once
+// the row has run out; the strip has max(row length) passes.  No plan to run:
+// each lane copies its own row, kPadFillU passes' loads in flight.
+constexpr int kPadFillU = 8;
+template <typename S, bool kSplit>
+__device__ bool pad_strip_fill_m1(int sa, int sb, int bits, long long limit, const uint32_t *__restrict__ packed,
+                                  const S *__restrict__ vh, const S *__restrict__ vl, long long out0,
+                                  uint32_t *__restrict__ pk_out, S *__restrict__ vo_h, S *__restrict__ vo_l) {
+  const int lane = threadIdx.x & 31;
+  int next;
+  int left = row_span(sa, sb, 32, (1u << bits) - 1, packed, lane, &next);
+  if (left < 0) left = 0;
+  for (long long p = 0; p < limit; p += kPadFillU) {
+    uint32_t c[kPadFillU];
+    S h[kPadFillU], l[kPadFillU];
+#pragma unroll
+    for (int u = 0; u < kPadFillU; ++u) {
+      c[u] = (uint32_t)lane;  // a zero item: column 0, this row
+      h[u] = S(0);
+      l[u] = S(0);
+      if (p + u < left) {
+        c[u] = packed[next + p + u];
+        h[u] = vh[next + p + u];
+        if (kSplit) l[u] = vl[next + p + u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPadFillU; ++u)
+      if (p + u < limit) {
+        const long long o = out0 + (p + u) * 32 + lane;
+        pk_out[o] = c[u];
+        vo_h[o] = h[u];
+        if (kSplit) vo_l[o] = l[u];
+      }
+  }
+  return __all_sync(kFull, left <= limit);
 }
 
 template <typename S, bool kSplit>
@@ -133,8 +206,15 @@ __global__ void __launch_bounds__(kPadWarps * 32) k_pad_fill(int strips, int hei
                                                             uint32_t *__restrict__ pk_out, S *__restrict__ vo_h,
                                                             S *__restrict__ vo_l) {
   const int nw = gridDim.x * kPadWarps;
-  for (int s = blockIdx.x * kPadWarps + (threadIdx.x >> 5); s < strips; s += nw)
-    pad_strip<true, S, kSplit>(s, height, bits, slots, sp, packed, vh, vl, sp_out[s], pk_out, vo_h, vo_l);
+  for (int s = blockIdx.x * kPadWarps + (threadIdx.x >> 5); s < strips; s += nw) {
+    const long long o0 = sp_out[s], o1 = sp_out[s + 1];
+    const long long limit = o1 > o0 ? (o1 - o0) / 32 : 0;
+    if (slots == 1)
+      pad_strip_fill_m1<S, kSplit>(sp[s], sp[s + 1], bits, limit, packed, vh, vl, o0, pk_out, vo_h, vo_l);
+    else
+      pad_strip_fill<S, kSplit>(sp[s], sp[s + 1], height, bits, slots, limit, packed, vh, vl, o0, pk_out, vo_h,
+                                vo_l);
+  }
 }
 
 size_t pad_ws_bytes(int strips) { return 256 + scan_ws_bytes(strips); }
