@@ -87,9 +87,14 @@ struct Encode<CMRS_BF16X2> {
 };
 
 // ---------------------------------------------------------------- packing
-// Section 4: packed = (col << bits) | (row mod height).  One warp per row.
-// Rows whose RowPtr range is invalid are skipped (the validation kernel has
-// flagged them), so no access leaves the arrays.
+// Section 4: packed = (col << bits) | (row mod height).  A warp takes 32
+// consecutive rows at a time: their entries are one contiguous CRS range,
+// walked with coalesced loads, kPackU batches of 32 in flight per lane; an
+// entry finds its row among the 32 row starts (held one per lane) by a
+// five-step shuffle search.  A group of rows with an invalid RowPtr range is
+// skipped (the validation kernel has flagged it), so no access leaves the
+// arrays.
+constexpr int kPackU = 4;
 template <typename In, int DT>
 __global__ void k_pack(int rows, int cols, int nnz, int height, int bits, const int32_t *__restrict__ row_ptr,
                        const int32_t *__restrict__ col_ind, const In *__restrict__ val_in,
@@ -97,19 +102,55 @@ __global__ void k_pack(int rows, int cols, int nnz, int height, int bits, const 
                        typename Encode<DT>::Out *__restrict__ vlo, StatusBlock *st) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
+  const long long groups = ((long long)rows + 31) / 32;
   uint32_t bad = 0;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += warps) {
-    int32_t a = row_ptr[i], b = row_ptr[i + 1];
-    if (a < 0 || b < a || b > nnz) continue;
-    uint32_t ris = (uint32_t)(i % height);
-    for (int32_t k = a + lane; k < b; k += 32) {
-      int32_t c = col_ind[k];
-      if (c < 0 || c >= cols) {
-        bad = 1;
-        c = 0;
+  for (long long g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups; g += warps) {
+    const long long r0 = g * 32;
+    const long long r = r0 + lane;
+    // row `lane` of the group: [start, end); rows past the matrix are empty
+    const int32_t start = r < rows ? row_ptr[r] : 0;
+    const int32_t last = row_ptr[min(r0 + 32, (long long)rows)];
+    int32_t end = __shfl_down_sync(0xffffffffu, start, 1);
+    if (lane == 31 || r + 1 >= rows) end = last;
+    const bool ok = r >= rows || (start >= 0 && end >= start && end <= nnz);
+    if (!__all_sync(0xffffffffu, ok)) continue;
+    const int32_t e0 = __shfl_sync(0xffffffffu, start, 0);
+    const int32_t e1 = last;
+    const int nrows = (int)min(32LL, rows - r0);
+    const int32_t key = lane < nrows ? start : e1;  // empty tail rows sort last
+    const uint32_t ris_lane = (uint32_t)(r % height);
+    for (int32_t k0 = e0; k0 < e1; k0 += 32 * kPackU) {
+      int32_t c[kPackU];
+      In v[kPackU];
+#pragma unroll
+      for (int u = 0; u < kPackU; ++u) {
+        const int32_t k = k0 + 32 * u + lane;
+        if (k < e1) {
+          c[u] = col_ind[k];
+          v[u] = val_in[k];
+        }
       }
-      packed[k] = ((uint32_t)c << bits) | ris;
-      Encode<DT>::put((double)val_in[k], vhi, vlo, k);
+#pragma unroll
+      for (int u = 0; u < kPackU; ++u) {
+        const int32_t k = k0 + 32 * u + lane;
+        // the row holding k: the last of the group's rows starting at or before k
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int32_t sj = __shfl_sync(0xffffffffu, key, j + step);
+          if (sj <= k) j += step;
+        }
+        const uint32_t ris = __shfl_sync(0xffffffffu, ris_lane, j);
+        if (k < e1) {
+          int32_t col = c[u];
+          if (col < 0 || col >= cols) {
+            bad = 1;
+            col = 0;
+          }
+          packed[k] = ((uint32_t)col << bits) | ris;
+          Encode<DT>::put((double)v[u], vhi, vlo, k);
+        }
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->status, ST_BAD_COL);
@@ -506,7 +547,7 @@ int from_csr_impl(int rows, int cols, int nnz, int height, int bits, uint32_t fl
   Out *vh = sorted ? reinterpret_cast<Out *>(ws + L.vtmp) : reinterpret_cast<Out *>(val_out);
   Out *vl = DT == CMRS_BF16X2 ? vh + cmrs_pad8(nnz) : nullptr;
   if (rows > 0 && nnz > 0) {
-    int g = (int)std::min<int64_t>(ceil_div((int64_t)rows * 32, 256), (int64_t)sms * 16);
+    int g = (int)std::min<int64_t>(ceil_div((int64_t)rows, 256), (int64_t)sms * 16);  // 8 warps x 32 rows
     k_pack<In, DT><<<g, 256, 0, st>>>(rows, cols, nnz, height, bits, row_ptr, col_ind, val_in, pk, vh, vl, sb);
     CMRS_LAUNCH_CHECK();
   }
