@@ -438,7 +438,11 @@ __global__ void __launch_bounds__(kRadixThreads) k_sort_long(int strips, int bit
 // over the strip's rows gives RowPtr[s*h + r] = StripPtr[s] + #(RIS < r).
 // Pass 2 scatters each entry to RowPtr[row] + (its rank among the strip's
 // entries of the same row, in strip order), a stable counting sort.
-template <typename V>
+// Unsorted strips (kSorted false) already hold their entries in CRS order:
+// the entry arrays are copied with the row bits dropped (coalesced, kPackU
+// batches in flight per lane) and RowPtr[s*h + r] is the first entry of
+// row r, found by a binary search of RowInStrip.
+template <typename V, bool kSorted>
 __global__ void k_to_csr(int rows, int nnz, int height, int bits, int strips, const int32_t *__restrict__ sp,
                          const uint32_t *__restrict__ packed, const V *__restrict__ vin, const V *__restrict__ vin_lo,
                          int32_t *__restrict__ row_ptr, int32_t *__restrict__ col_out, V *__restrict__ vout,
@@ -454,6 +458,47 @@ __global__ void k_to_csr(int rows, int nnz, int height, int bits, int strips, co
     const int32_t a = sp[s], b = sp[s + 1];
     const int64_t row0 = (int64_t)s * height;
     const int nrow = (int)std::min<int64_t>(height, rows - row0);
+    if (!kSorted) {
+      int32_t start = a;
+      if (lane > 0 && lane < nrow) {
+        int32_t lo = a, hi = b;
+        while (lo < hi) {
+          const int32_t mid = lo + ((hi - lo) >> 1);
+          if ((packed[mid] & mask) < (uint32_t)lane) lo = mid + 1;
+          else hi = mid;
+        }
+        start = lo;
+      }
+      if (lane < nrow) row_ptr[row0 + lane] = start;
+      for (int32_t i0 = a; i0 < b; i0 += 32 * kPackU) {
+        uint32_t p[kPackU];
+        V v[kPackU], vl[kPackU];
+#pragma unroll
+        for (int u = 0; u < kPackU; ++u) {
+          const int32_t i = i0 + 32 * u + lane;
+          if (i < b) {
+            p[u] = packed[i];
+            if (vout) {
+              v[u] = vin[i];
+              if (vout_lo) vl[u] = vin_lo[i];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kPackU; ++u) {
+          const int32_t i = i0 + 32 * u + lane;
+          if (i < b) {
+            if ((p[u] & mask) >= (uint32_t)nrow) bad = 1;
+            col_out[i] = (int32_t)(p[u] >> bits);
+            if (vout) {
+              vout[i] = v[u];
+              if (vout_lo) vout_lo[i] = vl[u];
+            }
+          }
+        }
+      }
+      continue;
+    }
     cnt[lane] = 0;
     __syncwarp();
     for (int32_t i = a + lane; i < b; i += 32) {
@@ -661,6 +706,17 @@ extern "C" int cmrs_to_csr_workspace(const cmrs_matrix *A, size_t *bytes) {
   return CMRS_OK;
 }
 
+template <typename V>
+void launch_to_csr(bool sorted, int g, cudaStream_t st, const cmrs_matrix *A, const V *vin, const V *vin_lo,
+                   int32_t *row_ptr, int32_t *col_out, V *vout, V *vout_lo, uint32_t *status) {
+  if (sorted)
+    k_to_csr<V, true><<<g, 256, 0, st>>>(A->rows, A->nnz, A->height, A->bits, A->strips, A->strip_ptr,
+                                         A->col_packed, vin, vin_lo, row_ptr, col_out, vout, vout_lo, status);
+  else
+    k_to_csr<V, false><<<g, 256, 0, st>>>(A->rows, A->nnz, A->height, A->bits, A->strips, A->strip_ptr,
+                                          A->col_packed, vin, vin_lo, row_ptr, col_out, vout, vout_lo, status);
+}
+
 extern "C" int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *col_ind_out, void *val_out,
                            void *workspace, size_t workspace_bytes, void *stream) {
   if (!A || !row_ptr_out || A->rows < 0 || A->nnz < 0) return CMRS_ERR_ARG;
@@ -678,27 +734,24 @@ extern "C" int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *
   }
   int g = (int)std::min<int64_t>(ceil_div((int64_t)A->strips * 32, 256), (int64_t)sms * 8);
   const int64_t lo_off = cmrs_pad8(A->nnz);
+  const bool sorted = (A->flags & CMRS_SORTED) != 0;
   switch (A->dtype) {
     case CMRS_F64:
-      k_to_csr<double><<<g, 256, 0, st>>>(A->rows, A->nnz, A->height, A->bits, A->strips, A->strip_ptr,
-                                          A->col_packed, (const double *)A->val, nullptr, row_ptr_out, col_ind_out,
-                                          (double *)val_out, nullptr, status);
+      launch_to_csr<double>(sorted, g, st, A, (const double *)A->val, nullptr, row_ptr_out, col_ind_out,
+                            (double *)val_out, nullptr, status);
       break;
     case CMRS_F32:
-      k_to_csr<float><<<g, 256, 0, st>>>(A->rows, A->nnz, A->height, A->bits, A->strips, A->strip_ptr,
-                                         A->col_packed, (const float *)A->val, nullptr, row_ptr_out, col_ind_out,
-                                         (float *)val_out, nullptr, status);
+      launch_to_csr<float>(sorted, g, st, A, (const float *)A->val, nullptr, row_ptr_out, col_ind_out,
+                           (float *)val_out, nullptr, status);
       break;
     case CMRS_BF16:
-      k_to_csr<uint16_t><<<g, 256, 0, st>>>(A->rows, A->nnz, A->height, A->bits, A->strips, A->strip_ptr,
-                                            A->col_packed, (const uint16_t *)A->val, nullptr, row_ptr_out,
-                                            col_ind_out, (uint16_t *)val_out, nullptr, status);
+      launch_to_csr<uint16_t>(sorted, g, st, A, (const uint16_t *)A->val, nullptr, row_ptr_out, col_ind_out,
+                              (uint16_t *)val_out, nullptr, status);
       break;
     case CMRS_BF16X2:
-      k_to_csr<uint16_t><<<g, 256, 0, st>>>(
-          A->rows, A->nnz, A->height, A->bits, A->strips, A->strip_ptr, A->col_packed, (const uint16_t *)A->val,
-          (const uint16_t *)A->val + lo_off, row_ptr_out, col_ind_out, (uint16_t *)val_out,
-          val_out ? (uint16_t *)val_out + lo_off : nullptr, status);
+      launch_to_csr<uint16_t>(sorted, g, st, A, (const uint16_t *)A->val, (const uint16_t *)A->val + lo_off,
+                              row_ptr_out, col_ind_out, (uint16_t *)val_out,
+                              val_out ? (uint16_t *)val_out + lo_off : nullptr, status);
       break;
   }
   CMRS_LAUNCH_CHECK();
