@@ -471,6 +471,7 @@ def run_ours(args):
         line["variants_f64"] = variant_sweep(b, a, xd, M_csr, flush, stream, bp)
         line["modified_cmrs"] = modified_cmrs(b, a, xd, rp, ci, va, flush, stream)
         line["heights_f64_row"] = height_sweep(b, a, xd, rp, ci, va, flush, stream)
+        line["strip_sorted_vs_unsorted_f64"] = sorted_strips(b, a, xd, rp, ci, va, flush, stream)
         line["conversion"] = conversion_times(b, a, rp, ci, va, M_csr, h,
                                               args.slots if args.variant == "padded" else None)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -592,6 +593,28 @@ def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
             b.cmrs_spmv(M64, xd, y, v, ws)
         ms = statistics.mean(time_steps(lambda: b.cmrs_spmv(M64, xd, y, v, ws), steps, flush, stream))
         out[name] = {"ms": ms, "gbs": bp / (ms / 1e3) / 1e9}
+    return out
+
+
+def sorted_strips(b, a, xd, rp, ci, va, flush, stream, steps=60):
+    """Section 4's fourth optimisation: the STRIP kernel (Algorithm 1) on
+    unsorted strips and on strips stably sorted by column, at heights 4 and 16
+    (FP64, beta+ of each height)."""
+    import torch
+    out = {}
+    y = torch.empty(a.rows, dtype=torch.float64, device=xd.device)
+    for h in (4, 16):
+        S = (a.rows + h - 1) // h
+        bp = 12 * a.nnz + 4 * S + 16 * a.rows
+        for tag, flags in (("unsorted", 0), ("sorted", b.CMRS_SORTED)):
+            M = b.cmrs_from_csr(rp, ci, va, a.cols, h, flags=flags, dtype=b.CMRS_F64)
+            ws = M.spmv_workspace(b.CMRS_VARIANT_STRIP)
+            for _ in range(3):
+                b.cmrs_spmv(M, xd, y, b.CMRS_VARIANT_STRIP, ws)
+            ms = statistics.mean(time_steps(lambda: b.cmrs_spmv(M, xd, y, b.CMRS_VARIANT_STRIP, ws), steps, flush,
+                                            stream))
+            out["h%d_%s" % (h, tag)] = {"ms": ms, "gbs": bp / (ms / 1e3) / 1e9}
+            del M
     return out
 
 

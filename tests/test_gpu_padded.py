@@ -133,6 +133,31 @@ def test_padded_degenerate(b):
         assert np.array_equal(b.cmrs_spmv(P, torch.from_numpy(x).cuda()).cpu().numpy(), x)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_padded_short_strips(b, dtype):
+    """M = 1 matrices of one or two passes per strip on average (like the
+    paper's p7): rows of 0..2 entries, runs of empty strips, one longer row, a
+    ragged last strip; also reordered and written back through a row map."""
+    L = np.random.default_rng(dtype).integers(0, 2, 70001)
+    L[::97] = 2
+    L[100:300] = 0
+    L[5000] = 90
+    a = inputs.from_lengths(L, 80000, seed=dtype + 20)
+    P = b.cmrs_pad(convert(b, a, 32, dtype), 1)
+    assert P.nnz <= 64 * P.struct.strips
+    x = xvec(a, dtype)
+    check_spmv(b, P, a, x, b.CMRS_VARIANT_PADDED, dtype)
+    rp = torch.from_numpy(a.row_ptr).cuda()
+    perm = b.cmrs_row_order(rp, 1024)
+    rp2, ci2, v2 = b.cmrs_permute_csr(rp, torch.from_numpy(a.col_ind).cuda(), torch.from_numpy(a.val).cuda(), perm)
+    Q = b.cmrs_pad(b.cmrs_from_csr(rp2, ci2, v2, a.cols, 32, dtype=dtype), 1)
+    y = b.cmrs_spmv_rows(Q, torch.from_numpy(x).cuda(), perm).cpu().numpy().astype(np.float64)
+    vq = orc.decode(orc.encode(a.val, dtype), dtype, a.nnz) if dtype else a.val.astype(np.float64)
+    yref, absy = orc.csr_spmv(a.row_ptr, a.col_ind, vq, x.astype(np.float64))
+    tol = 1e-12 * absy if dtype == 0 else (np.diff(a.row_ptr) + 2) * 2.0**-24 * absy
+    assert np.all(np.abs(y - yref) <= tol)
+
+
 def test_padded_rejections(b):
     a = skewed(3, 2000)
     M = convert(b, a, 16)

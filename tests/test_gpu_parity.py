@@ -318,6 +318,9 @@ def test_paper_extra_matrices(b, which):
         M = convert(b, a, h)
         for var in VARIANTS:
             check_spmv(b, M, a, x, var, 0)
+    # the bench's forms: p7 at height 32, one slot (one pass per strip); dense4 at height 4, 8 slots
+    P = b.cmrs_pad(convert(b, a, 32 if which == "p7" else 4), 1 if which == "p7" else 8)
+    check_spmv(b, P, a, x, b.CMRS_VARIANT_PADDED, 0)
 
 
 @pytest.mark.parametrize("case", ["stencil", "short", "long", "skewed", "sorted"])
