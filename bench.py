@@ -60,6 +60,9 @@ def args_parse():
                    help="stencil27 is the headline; the others print the same JSON schema for their workload")
     p.add_argument("--batch-count", type=int, default=256, help="batched workload: matrices (256 = full size)")
     p.add_argument("--window", type=int, default=0, help="irregular workload: row-reordering window (0: none)")
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16", "bf16x2"],
+                   help="stencil27: stored value form of the measured line (x and y FP32 unless f64)")
+    p.add_argument("--grid", type=int, default=128, help="stencil27: grid edge (128 = the full workload)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary storage-form measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return p.parse_args()
@@ -371,6 +374,7 @@ def time_steps(fn, steps, flush, stream):
 
 
 def run_ours(args):
+    import numpy as np
     import torch
     rank, world, dist = dist_setup(args.gpus)
     from paper_1203_2946_gb300 import build
@@ -380,19 +384,28 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     variant = binding_variant = dict(b.VARIANTS, auto=b.CMRS_VARIANT_AUTO,
                                      padded=b.CMRS_VARIANT_PADDED)[args.variant]
-    a, x = inputs.workload_stencil27_128()
+    g = args.grid
+    if g == 128:
+        a, x = inputs.workload_stencil27_128()
+    else:
+        a = inputs.stencil_3d_27pt(g, g, g, seed=1)
+        x = inputs.uniform_vector(a.cols, 0)
+    dt = {"f64": b.CMRS_F64, "f32": b.CMRS_F32, "bf16": b.CMRS_BF16, "bf16x2": b.CMRS_BF16X2}[args.dtype]
+    s_v = {b.CMRS_F64: 8, b.CMRS_F32: 4, b.CMRS_BF16: 2, b.CMRS_BF16X2: 4}[dt]  # stored value bytes
+    s_x = 8 if dt == b.CMRS_F64 else 4                                          # x and y element bytes
     h = args.height
     strips = (a.rows + h - 1) // h
     rp = torch.from_numpy(a.row_ptr).to(dev)
     ci = torch.from_numpy(a.col_ind).to(dev)
     va = torch.from_numpy(a.val).to(dev)
-    M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F64)
+    M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=dt)
     M_csr = M
     if args.variant == "padded":
         M = b.cmrs_pad(M, args.slots)  # Section 6.6 arrangement; bytes_per_step stays the unpadded beta+
     variant = b.cmrs_spmv_variant(M, binding_variant)
-    xd = torch.from_numpy(x).to(dev)
-    yd = torch.empty(a.rows, dtype=torch.float64, device=dev)
+    xv = x if dt == b.CMRS_F64 else x.astype(np.float32)
+    xd = torch.from_numpy(xv).to(dev)
+    yd = torch.empty(a.rows, dtype=torch.float64 if dt == b.CMRS_F64 else torch.float32, device=dev)
     ws = M.spmv_workspace(variant)
     flush = L2Flush(dev)
 
@@ -402,7 +415,7 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    bp = beta_plus(a.nnz, a.rows, strips, 8)
+    bp = (s_v + 4) * a.nnz + 4 * strips + 2 * s_x * a.rows  # beta+ (Eq. 6.1), x and y in their own width
     peak, peak_kind = measured_peaks()
     pci = None
     try:
@@ -423,8 +436,8 @@ def run_ours(args):
     b.cmrs_spmv_check(M, variant)
 
     # e2e through the C ABI with host buffers (x in, y out every step, pipelined)
-    xh = torch.from_numpy(x).pin_memory()
-    yhs = [torch.empty(a.rows, dtype=torch.float64).pin_memory() for _ in range(2)]
+    xh = torch.from_numpy(xv).pin_memory()
+    yhs = [torch.empty(a.rows, dtype=yd.dtype).pin_memory() for _ in range(2)]
     xds = [xd, torch.empty_like(xd)]
     yds = [yd, torch.empty_like(yd)]
     e2e_steps = max(20, min(args.steps, 200))
@@ -432,12 +445,16 @@ def run_ours(args):
                                                 yds, yhs, e2e_steps))
 
     kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[variant]
+    if variant == 3 and args.slots == 1 and dt != b.CMRS_F64:
+        kname = "k_spmv_padded_bulk"  # the library stages the narrow forms' M = 1 walk through shared memory
+    form = {"f64": "FP64 values and x", "f32": "FP32 values, x and y", "bf16": "BF16 values, FP32 x and y",
+            "bf16x2": "split-BF16 values, FP32 x and y"}[args.dtype]
     trimmed = sorted(times)[:-1] if len(times) > 1 else times
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "27-point stencil 128^3 (n=2097152, nnz=55742968), FP64 values and x, "
+        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": "27-point stencil %d^3 (n=%d, nnz=%d), %s, " % (g, a.rows, a.nnz, form)
                                + ("modified CMRS (Section 6.6) h=%d, M=%d slot(s) per row per pass" % (h, args.slots)
                                   if args.variant == "padded" else "CMRS h=%d, variant %s" % (h, args.variant)),
                    "height": h, "variant": args.variant, "bytes_per_step": bp,
@@ -447,17 +464,17 @@ def run_ours(args):
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU"},
         "gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
         "gflops_paper": (2 * a.nnz - a.rows) / (per_ms / 1e3) / 1e9,
-        "eta": eta(a.nnz, a.rows, strips, 8, per_ms, peak),
+        "eta": eta(a.nnz, a.rows, strips, 8, per_ms, peak) if dt == b.CMRS_F64 else None,
         "pct_of_hbm_peak": 100.0 * (value / world) / peak,
         "pct_of_nominal_8tbs": 100.0 * (value / world) / 8000.0,
         "paper_protocol": {"mean_ms": statistics.mean(trimmed), "std_ms": statistics.pstdev(trimmed),
                            "min_ms": min(times)},
         "roofline": {"bound": "hbm", "achieved": bp / (per_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": bp / (per_ms / 1e3) / 1e9 / peak, "peak_kind": peak_kind + " (hbm_gbs)",
-                     "traffic": traffic_record(kname, "stencil27_128_f64_h%d" % h + (
+                     "traffic": traffic_record(kname, "stencil27_%d_%s_h%d" % (g, args.dtype, h) + (
                          "_m%d" % args.slots if args.variant == "padded" else "")), "kernel": kname},
         "e2e": {"value": world * bp / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
-                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(a.rows * 8),
+                "h2d_bytes_per_step": int(xv.nbytes), "d2h_bytes_per_step": int(a.rows * s_x),
                 "ms_per_step": e2e_ms, "note": "x host->device, cmrs_spmv, y device->host every step, "
                 "pipelined over two buffer pairs (copy-in, product and copy-out of neighbouring steps overlap); "
                 "matrix resident"},
@@ -465,7 +482,7 @@ def run_ours(args):
         "clocks": sampler.summary(),
         "wall_s_timed_region": wall,
     }
-    if rank == 0 and not args.no_extras and world == 1:
+    if rank == 0 and not args.no_extras and world == 1 and dt == b.CMRS_F64 and g == 128:
         line["forms"] = storage_forms(b, a, x, rp, ci, va, h, flush, stream, per_ms,
                                       args.slots if args.variant == "padded" else None)
         line["variants_f64"] = variant_sweep(b, a, xd, M_csr, flush, stream, bp)

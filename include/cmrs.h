@@ -292,9 +292,11 @@ int cmrs_spmv_rows(const cmrs_matrix *A, const void *x, void *y, const int32_t *
  * their results are undefined.  Asynchronous on `stream`. */
 int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, void *stream);
 
-/* Error status left by the last bounded in-kernel wait on this device's
- * status word inside `workspace` (CMRS_OK or CMRS_ERR_TIMEOUT).  Reads device
- * memory synchronously on `stream`. */
+/* Error status the SpMV kernels left in the status word inside `workspace`,
+ * then cleared: CMRS_ERR_TIMEOUT if a bounded in-kernel wait gave up,
+ * CMRS_ERR_ARG if a padded strip was not a whole number of 32-item passes
+ * (a matrix not made by cmrs_pad_fill; that strip's rows are not valid),
+ * else CMRS_OK.  Reads device memory synchronously on `stream`. */
 int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, void *stream);
 
 /* ---- multi right-hand-side SpMM, single and batched ----------------------

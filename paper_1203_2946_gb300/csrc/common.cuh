@@ -35,6 +35,7 @@ enum : uint32_t {
   ST_BAD_COL = 2u,
   ST_BAD_RIS = 4u,
   ST_TIMEOUT = 8u,
+  ST_BAD_PAD = 16u,  // a padded strip not made of whole 32-item passes
 };
 
 // ------------------------------------------------------------------ device side

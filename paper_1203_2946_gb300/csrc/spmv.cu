@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cmrs {
@@ -783,6 +785,163 @@ __global__ void k_merge_fixup(int ntiles, int rows, const TileRec *__restrict__ 
   if (row >= 0 && row < rows) y[row] = sum;
 }
 
+// ============================================================== PADDED bulk-staged mapping
+// Bulk-staged walk for M = 1 (height 32).  One lane per warp copies the
+// warp's strips, kPadCh passes at a time, into a two-stage shared-memory ring
+// (cp.async.bulk, completion counted on a per-stage mbarrier, L2 evict-first),
+// one stage ahead of the lanes, which then read pass p's item j at word
+// 32 p + j of the stage: DRAM sees whole chunks of each stream instead of a
+// 128-byte line per warp load.  The next strip's bounds are read one strip
+// ahead.  Waits are bounded: on a timeout the warp sets ST_TIMEOUT, waits
+// (bounded) for the copies it has in flight, and leaves.
+#ifndef CMRS_PAD_CH
+#define CMRS_PAD_CH 16
+#endif
+#ifndef CMRS_PAD_BULK_WARPS
+#define CMRS_PAD_BULK_WARPS 8
+#endif
+#ifndef CMRS_PAD_BULK
+#define CMRS_PAD_BULK 14  // bit DT set: that value type's M = 1 form takes this walk (FP32, BF16, split BF16)
+#endif
+constexpr int kPadCh = CMRS_PAD_CH;
+constexpr int kPadBulkWarps = CMRS_PAD_BULK_WARPS;
+template <int DT>
+struct PadRing {
+  typedef typename Form<DT>::Stored S;
+  static constexpr bool kSplit = DT == CMRS_BF16X2;
+  static constexpr size_t kPk = (size_t)kPadCh * 32 * 4;
+  static constexpr size_t kV = (size_t)kPadCh * 32 * sizeof(S);
+  static constexpr size_t kStage = kPk + kV * (kSplit ? 2 : 1);
+};
+
+template <int DT>
+__global__ void __launch_bounds__(kPadBulkWarps * 32) k_spmv_padded_bulk(
+    int rows, int bits, int strips, const int32_t *__restrict__ sp, const uint32_t *__restrict__ packed,
+    const typename Form<DT>::Stored *__restrict__ hi, const typename Form<DT>::Stored *__restrict__ lo,
+    const typename Form<DT>::Acc *__restrict__ x, typename Form<DT>::Acc *__restrict__ y,
+    const int32_t *__restrict__ row_map, uint32_t *status) {
+  typedef typename Form<DT>::Acc A;
+  typedef typename Form<DT>::Stored S;
+  typedef PadRing<DT> R;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ uint64_t bars_all[kPadBulkWarps][2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  char *ring = smem + (size_t)w * 2 * R::kStage;
+  uint64_t *bar = bars_all[w];
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  uint64_t pol = 0;
+  if (lane == 0) pol = policy_evict_first();
+  const int nw = gridDim.x * kPadBulkWarps;
+  // copy cursor: strip ps, items [pk, pe); strip ps + nw has bounds [nk, ne)
+  int ps = blockIdx.x * kPadBulkWarps + w, pk = 0, pe = 0, nk = 0, ne = 0;
+  if (ps < strips) {
+    pk = sp[ps];
+    pe = sp[ps + 1];
+  }
+  if (ps + nw < strips) {
+    nk = sp[ps + nw];
+    ne = sp[ps + nw + 1];
+  }
+  int cs[2] = {0, 0}, cn[2] = {0, 0};
+  bool clast[2] = {false, false}, valid[2] = {false, false};
+  uint32_t par[2] = {0u, 0u};
+  uint32_t bad = 0;
+  // The stage index is a compile-time constant in both lambdas (the ring
+  // loop alternates step(0), step(1)), so the descriptors stay in registers.
+  auto issue = [&](auto stc) {  // next chunk into stage st (warp-uniform; lane 0 copies)
+    constexpr int st = decltype(stc)::value;
+    const int n = max(0, min(kPadCh * 32, pe - pk));
+    const bool whole = ((pk | n) & 31) == 0;  // padded strips hold whole 32-item passes
+    if (!whole) bad = 1;
+    cs[st] = ps;
+    cn[st] = whole ? n : 0;
+    if (lane == 0) {
+      char *dst = ring + st * R::kStage;
+      const uint32_t m = (uint32_t)cn[st];
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bar[st], m * (4u + (uint32_t)sizeof(S) * (R::kSplit ? 2u : 1u)));
+      if (m) {
+        bulk_g2s(dst, packed + pk, m * 4u, &bar[st], pol);
+        bulk_g2s(dst + R::kPk, hi + pk, m * (uint32_t)sizeof(S), &bar[st], pol);
+        if (R::kSplit) bulk_g2s(dst + R::kPk + R::kV, lo + pk, m * (uint32_t)sizeof(S), &bar[st], pol);
+      }
+    }
+    valid[st] = true;
+    pk += n;
+    clast[st] = pk >= pe;
+    if (clast[st]) {  // on to the warp's next strip, whose bounds were read one strip ago
+      ps += nw;
+      pk = nk;
+      pe = ne;
+      nk = ne = 0;
+      if (ps + nw < strips) {
+        nk = sp[ps + nw];
+        ne = sp[ps + nw + 1];
+      }
+    }
+  };
+  A acc = A(0);
+  // one ring step on stage st: 0 = go on, 1 = no chunk left, 2 = a wait timed out
+  auto step = [&](auto stc) -> int {
+    constexpr int st = decltype(stc)::value;
+    if (!valid[st]) return 1;
+    if (ps < strips) issue(std::integral_constant<int, st ^ 1>());
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], par[st]));
+    par[st] ^= 1u;
+    if (!ok) {
+      if (lane == 0) atomicOr(status, ST_TIMEOUT);
+      mbar_wait_bounded(&bar[st], par[st] ^ 1u);  // copies still in flight land before the warp leaves
+      if (valid[st ^ 1]) mbar_wait_bounded(&bar[st ^ 1], par[st ^ 1]);
+      return 2;
+    }
+    const uint32_t *cp = reinterpret_cast<const uint32_t *>(ring + st * R::kStage);
+    const S *vh = reinterpret_cast<const S *>(ring + st * R::kStage + R::kPk);
+    const S *vl = reinterpret_cast<const S *>(ring + st * R::kStage + R::kPk + R::kV);
+    const int np = cn[st] >> 5;
+    for (int p0 = 0; p0 < np; p0 += kPadU) {
+      uint32_t c[kPadU];
+      A v[kPadU], xv[kPadU];
+#pragma unroll
+      for (int u = 0; u < kPadU; ++u)
+        if (p0 + u < np) {
+          const int i = (p0 + u) * 32 + lane;
+          c[u] = cp[i];
+          v[u] = Form<DT>::value(vh, vl, i);
+        }
+#pragma unroll
+      for (int u = 0; u < kPadU; ++u)
+        if (p0 + u < np) xv[u] = ld_x(x + (c[u] >> bits));
+#pragma unroll
+      for (int u = 0; u < kPadU; ++u)
+        if (p0 + u < np) acc = fma_acc(v[u], xv[u], acc);
+    }
+    if (clast[st]) {
+      const long long row = (long long)cs[st] * 32 + lane;
+      if (row < rows) {
+        const long long t = row_map ? row_map[row] : row;
+        if (t >= 0 && t < rows) y[t] = acc;
+      }
+      acc = A(0);
+    }
+    __syncwarp();
+    valid[st] = false;
+    return 0;
+  };
+  if (ps < strips) issue(std::integral_constant<int, 0>());
+  int rc = 0;
+  while (rc == 0) {
+    rc = step(std::integral_constant<int, 0>());
+    if (rc == 0) rc = step(std::integral_constant<int, 1>());
+  }
+  if (rc == 2) return;
+  if (bad && lane == 0) atomicOr(status, ST_BAD_PAD);
+}
+
 // ============================================================== host side
 struct Occ {
   std::mutex mu;
@@ -813,8 +972,21 @@ size_t merge_ws_bytes(int nnz) {
 template <int DT, int kM>
 int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, const typename Form<DT>::Stored *lo,
                   const typename Form<DT>::Acc *x, typename Form<DT>::Acc *y, const int32_t *row_map,
-                  cudaStream_t st) {
+                  uint32_t *status, cudaStream_t st) {
   typedef typename Form<DT>::Acc Acc;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(hi) |
+                         reinterpret_cast<uintptr_t>(lo)) & 15) == 0;
+  if (kM == 1 && ((CMRS_PAD_BULK >> DT) & 1) && aligned) {
+    static Occ occ_bulk;
+    const size_t smem = (size_t)kPadBulkWarps * 2 * PadRing<DT>::kStage;
+    const int per_sm = occupancy(k_spmv_padded_bulk<DT>, kPadBulkWarps * 32, smem, occ_bulk);
+    const long long need = ceil_div(A->strips, kPadBulkWarps);
+    const int grid = (int)std::min<long long>(need, (long long)per_sm * sm_count());
+    k_spmv_padded_bulk<DT><<<grid, kPadBulkWarps * 32, smem, st>>>(A->rows, A->bits, A->strips, A->strip_ptr,
+                                                                   A->col_packed, hi, lo, x, y, row_map, status);
+    CMRS_LAUNCH_CHECK();
+    return CMRS_OK;
+  }
   static Occ occ;
   const size_t smem = (size_t)kPadWarps * kM * A->height * sizeof(Acc);
   const int per_sm = occupancy(k_spmv_padded<DT, kM>, kPadWarps * 32, (size_t)kPadWarps * kM * 32 * sizeof(Acc), occ);
@@ -857,10 +1029,10 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
     CMRS_LAUNCH_CHECK();
   } else if (variant == CMRS_VARIANT_PADDED) {
     switch (CMRS_PAD_SLOTS_OF(A->flags)) {
-      case 1: return launch_padded<DT, 1>(A, hi, lo, x, y, row_map, st);
-      case 2: return launch_padded<DT, 2>(A, hi, lo, x, y, row_map, st);
-      case 4: return launch_padded<DT, 4>(A, hi, lo, x, y, row_map, st);
-      default: return launch_padded<DT, 8>(A, hi, lo, x, y, row_map, st);
+      case 1: return launch_padded<DT, 1>(A, hi, lo, x, y, row_map, status, st);
+      case 2: return launch_padded<DT, 2>(A, hi, lo, x, y, row_map, status, st);
+      case 4: return launch_padded<DT, 4>(A, hi, lo, x, y, row_map, status, st);
+      default: return launch_padded<DT, 8>(A, hi, lo, x, y, row_map, status, st);
     }
   } else {
     static Occ occ;
@@ -1017,6 +1189,10 @@ extern "C" int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *wo
   if (s & ST_TIMEOUT) {
     CMRS_CUDA_TRY(cudaMemsetAsync(const_cast<void *>(workspace), 0, 4, st));
     return CMRS_ERR_TIMEOUT;
+  }
+  if (s & ST_BAD_PAD) {
+    CMRS_CUDA_TRY(cudaMemsetAsync(const_cast<void *>(workspace), 0, 4, st));
+    return CMRS_ERR_ARG;
   }
   return CMRS_OK;
 }
