@@ -803,6 +803,12 @@ __global__ void k_merge_fixup(int ntiles, int rows, const TileRec *__restrict__ 
 #ifndef CMRS_PAD_BULK
 #define CMRS_PAD_BULK 14  // bit DT set: that value type's M = 1 form takes this walk (FP32, BF16, split BF16)
 #endif
+#ifndef CMRS_PAD_BULK_MIN_PASSES
+#define CMRS_PAD_BULK_MIN_PASSES 12  // ... when its strips average at least this many passes (BF16 forms)
+#endif
+#ifndef CMRS_PAD_BULK_MIN_PASSES_F32
+#define CMRS_PAD_BULK_MIN_PASSES_F32 16  // the same for FP32 values
+#endif
 constexpr int kPadCh = CMRS_PAD_CH;
 constexpr int kPadBulkWarps = CMRS_PAD_BULK_WARPS;
 template <int DT>
@@ -976,7 +982,9 @@ int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, con
   typedef typename Form<DT>::Acc Acc;
   const bool aligned = ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(hi) |
                          reinterpret_cast<uintptr_t>(lo)) & 15) == 0;
-  if (kM == 1 && ((CMRS_PAD_BULK >> DT) & 1) && aligned) {
+  // short strips (a pass or a few) pay a copy round trip each: the plain walk is faster there
+  const long long min_passes = DT == CMRS_F32 ? CMRS_PAD_BULK_MIN_PASSES_F32 : CMRS_PAD_BULK_MIN_PASSES;
+  if (kM == 1 && ((CMRS_PAD_BULK >> DT) & 1) && aligned && (long long)A->nnz >= 32LL * min_passes * A->strips) {
     static Occ occ_bulk;
     const size_t smem = (size_t)kPadBulkWarps * 2 * PadRing<DT>::kStage;
     const int per_sm = occupancy(k_spmv_padded_bulk<DT>, kPadBulkWarps * 32, smem, occ_bulk);
