@@ -803,12 +803,6 @@ __global__ void k_merge_fixup(int ntiles, int rows, const TileRec *__restrict__ 
 #ifndef CMRS_PAD_BULK
 #define CMRS_PAD_BULK 14  // bit DT set: that value type's M = 1 form takes this walk (FP32, BF16, split BF16)
 #endif
-#ifndef CMRS_PAD_BULK_MIN_PASSES
-#define CMRS_PAD_BULK_MIN_PASSES 12  // ... when its strips average at least this many passes (BF16 forms)
-#endif
-#ifndef CMRS_PAD_BULK_MIN_PASSES_F32
-#define CMRS_PAD_BULK_MIN_PASSES_F32 16  // the same for FP32 values
-#endif
 constexpr int kPadCh = CMRS_PAD_CH;
 constexpr int kPadBulkWarps = CMRS_PAD_BULK_WARPS;
 template <int DT>
@@ -974,6 +968,15 @@ size_t merge_ws_bytes(int nnz) {
   const long long ntiles = ceil_div(nnz, kMergeTile);
   return 256 + align256((size_t)(ntiles + 1) * 4) + align256((size_t)ntiles * sizeof(TileRec));
 }
+
+// The staged walk (k_spmv_padded_bulk) is taken by the value forms CMRS_PAD_BULK
+// names when the strips average at least this many passes (BF16 forms; FP32)
+#ifndef CMRS_PAD_BULK_MIN_PASSES
+#define CMRS_PAD_BULK_MIN_PASSES 12
+#endif
+#ifndef CMRS_PAD_BULK_MIN_PASSES_F32
+#define CMRS_PAD_BULK_MIN_PASSES_F32 16
+#endif
 
 template <int DT, int kM>
 int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, const typename Form<DT>::Stored *lo,
