@@ -51,7 +51,7 @@ def args_parse():
     p.add_argument("--height", type=int, default=None,
                    help="strip height (default: 32 for the 27-point headline, power-law and p7; else 4)")
     p.add_argument("--slots", type=int, default=None, help="padded variant: slots per row per warp pass (M of "
-                   "Section 6.6; 1, 2, 4 or 8; default 1, irregular 2, dense4 8)")
+                   "Section 6.6; 1, 2, 4 or 8; default 1, irregular 2, dense4 4)")
     p.add_argument("--variant", default=None, choices=["row", "strip", "merge", "auto", "padded"],
                    help="SpMV kernel variant (default: padded for the 27-point headline, p7 and dense4; "
                         "power-law merge; else row)")
@@ -445,7 +445,10 @@ def run_ours(args):
                                                 yds, yhs, e2e_steps))
 
     kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[variant]
-    if variant == 3 and args.slots == 1 and dt != b.CMRS_F64:
+    split = variant == 3 and ws.numel() > 256  # a padded workspace past the status word: strips split over warps
+    if split:
+        kname = "k_spmv_padded_split"  # + k_pad_combine
+    elif variant == 3 and args.slots == 1 and dt != b.CMRS_F64:
         kname = "k_spmv_padded_bulk"  # the library stages the narrow forms' M = 1 walk through shared memory
     form = {"f64": "FP64 values and x", "f32": "FP32 values, x and y", "bf16": "BF16 values, FP32 x and y",
             "bf16x2": "split-BF16 values, FP32 x and y"}[args.dtype]
@@ -478,7 +481,7 @@ def run_ours(args):
                 "ms_per_step": e2e_ms, "note": "x host->device, cmrs_spmv, y device->host every step, "
                 "pipelined over two buffer pairs (copy-in, product and copy-out of neighbouring steps overlap); "
                 "matrix resident"},
-        "gpu_launches": args.steps * (3 if variant == 2 else 1),
+        "gpu_launches": args.steps * (3 if variant == 2 else 2 if split else 1),
         "clocks": sampler.summary(),
         "wall_s_timed_region": wall,
     }
@@ -641,10 +644,10 @@ def main():
         args.variant = {"stencil27": "padded", "powerlaw": "merge", "p7": "padded", "dense4": "padded"}.get(
             args.workload, "row")
     if args.height is None:
-        args.height = 4 if args.workload == "dense4" else (
+        args.height = 8 if args.workload == "dense4" else (
             32 if args.workload in ("powerlaw", "p7") or args.variant == "padded" else 4)
     if args.slots is None:
-        args.slots = {"irregular": 2, "dense4": 8}.get(args.workload, 1)
+        args.slots = {"irregular": 2, "dense4": 4}.get(args.workload, 1)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stencil27":
@@ -738,6 +741,18 @@ def run_secondary(args):
                 vms = statistics.mean(time_steps(g, 20, flush, stream))
                 var[vn] = {"ms": vms, "gbs": bp / (vms / 1e3) / 1e9}
             extra["variants_f64"] = var
+            if args.workload == "dense4" and args.variant == "padded":
+                pads = {}  # the other padded forms (few long strips: each strip split over several warps)
+                for ph, pm in ((4, 8), (8, 4), (16, 2), (32, 1)):
+                    Q = b.cmrs_pad(b.cmrs_from_csr(rp, ci, va, a.cols, ph, dtype=b.CMRS_F64), pm)
+                    qws = Q.spmv_workspace(b.CMRS_VARIANT_PADDED)
+                    g = lambda: b.cmrs_spmv(Q, xd, yd, b.CMRS_VARIANT_PADDED, qws)  # noqa: E731
+                    for _ in range(2):
+                        g()
+                    qms = statistics.mean(time_steps(g, 20, flush, stream))
+                    pads["h%d_m%d" % (ph, pm)] = {"ms": qms, "gbs": bp / (qms / 1e3) / 1e9}
+                    del Q
+                extra["padded_forms_f64"] = pads
             fn()
         if args.workload == "powerlaw":
             forms = {}
@@ -766,6 +781,9 @@ def run_secondary(args):
         e_ms = e2e_pipelined(lambda xv, yv: b.cmrs_spmv(M, xv, yv, v, ws), xh, [xd, torch.empty_like(xd)],
                              [yd, torch.empty_like(yd)], yhs, max(20, min(steps, 200)))
         kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[ran]
+        split = ran == 3 and ws.numel() > 256  # a padded workspace past the status word: strips split over warps
+        if split:
+            kname = "k_spmv_padded_split"  # + k_pad_combine
         line = _line(args, gbs, "GB/s", per_ms, name,
                      {"workload": wl, "height": h, "variant": args.variant,
                       "kernel_variant": ("row", "strip", "merge", "padded")[ran], "bytes_per_step": bp,
@@ -774,7 +792,7 @@ def run_secondary(args):
                       "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": kname},
                      {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(x.nbytes),
                       "d2h_bytes_per_step": int(a.rows * x.itemsize), "ms_per_step": e_ms},
-                     steps * (3 if ran == 2 else 1), sampler.summary(), extra)
+                     steps * (3 if ran == 2 else 2 if split else 1), sampler.summary(), extra)
         print(json.dumps(line), flush=True)
         return
 

@@ -248,9 +248,14 @@ int cmrs_permute_csr(int rows, int nnz, const int32_t *row_ptr, const int32_t *c
  * writes are still kept inside y.  variant: CMRS_VARIANT_*.  ROW and MERGE
  * need col_packed and val 16-byte aligned (CMRS_ERR_ARG otherwise).
  * workspace: >= cmrs_spmv_workspace() bytes, 256-byte aligned (may be NULL
- * when the query returns 0).  The result depends only on A, x and the variant
- * (fixed summation order, no atomics on values): repeated calls give
- * bit-identical y. */
+ * when the query returns 0).  For a padded matrix of few long strips (fewer
+ * than two per resident warp, at least 64 passes each on average) the query
+ * includes room for per-part row sums: each strip is then split over several
+ * warps and a second kernel adds each row's parts in order; with a workspace
+ * of only 256 bytes the one-warp-per-strip walk runs instead.  The result
+ * depends only on A, x, the variant and (padded matrices) whether the
+ * workspace holds the part sums and the device's SM count: fixed summation
+ * order, no atomics on values, so repeated calls give bit-identical y. */
 int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes);
 
 /* The kernel variant cmrs_spmv runs for `variant` (resolves

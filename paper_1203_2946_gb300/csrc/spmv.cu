@@ -785,6 +785,127 @@ __global__ void k_merge_fixup(int ntiles, int rows, const TileRec *__restrict__ 
   if (row >= 0 && row < rows) y[row] = sum;
 }
 
+// ============================================================== PADDED split-strip mapping
+// A padded matrix with few, long strips (the dense rows of dense4: 2,500
+// strips of 1,250 passes) leaves most warps idle with one warp per strip.
+// Here each strip's passes are cut into P parts of near-equal length, one
+// warp per (strip, part); a warp sums its part exactly as k_spmv_padded does
+// (register at M = 1, slot buffer at M > 1) and writes the partial sum of each
+// of the strip's rows to part[(s P + p) h + r]; k_pad_combine then adds a
+// row's P partials in part order and writes y -- the same result on every
+// call.
+#ifndef CMRS_PAD_SPLIT_MINB
+#define CMRS_PAD_SPLIT_MINB 5  // resident CTAs per SM asked of the register allocator (6 spills at FP64)
+#endif
+template <int DT, int kM>
+__global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_SPLIT_MINB) k_spmv_padded_split(
+    int height, int bits, int strips, int P, const int32_t *__restrict__ sp, const uint32_t *__restrict__ packed,
+    const typename Form<DT>::Stored *__restrict__ hi, const typename Form<DT>::Stored *__restrict__ lo,
+    const typename Form<DT>::Acc *__restrict__ x, typename Form<DT>::Acc *__restrict__ part) {
+  typedef typename Form<DT>::Acc A;
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  A *buf = reinterpret_cast<A *>(smem) + (size_t)w * kM * height;
+  const uint32_t mask = (1u << bits) - 1;
+  const int slot = lane & (kM - 1);
+  const uint64_t pol = policy_evict_first();
+  const long long nw = (long long)gridDim.x * kPadWarps;
+  int h2 = 1;
+  while (h2 < height) h2 <<= 1;
+  const int G = kM < 32 / h2 ? kM : 32 / h2;  // lanes summing one row's slots
+  const int per = kM / G;
+  if (kM > 1) {  // zeroed here, then by each unit's slot sum
+    for (int i = lane; i < kM * height; i += 32) buf[i] = A(0);
+    __syncwarp();
+  }
+  const long long units = (long long)strips * P;
+  for (long long u = (long long)blockIdx.x * kPadWarps + w; u < units; u += nw) {
+    const int s = (int)(u / P), p = (int)(u - (long long)s * P);
+    const int a0 = sp[s], L = (sp[s + 1] - a0) >> 5;  // the strip's passes
+    const int a = a0 + 32 * (int)((long long)L * p / P), b = a0 + 32 * (int)((long long)L * (p + 1) / P);
+    A acc = A(0);
+    for (int k0 = a; k0 < b; k0 += 32 * kPadU) {
+      uint32_t c[kPadU];
+      A v[kPadU], xv[kPadU];
+#pragma unroll
+      for (int j = 0; j < kPadU; ++j)
+        if (k0 + 32 * j < b) {  // warp-uniform
+          const long long k = (long long)k0 + 32 * j + lane;
+          c[j] = ld_stream(packed + k, pol);
+          v[j] = ld_val_stream<DT>(hi, lo, k, pol);
+        }
+#pragma unroll
+      for (int j = 0; j < kPadU; ++j)
+        if (k0 + 32 * j < b) xv[j] = ld_x(x + (c[j] >> bits));
+#pragma unroll
+      for (int j = 0; j < kPadU; ++j)
+        if (k0 + 32 * j < b) {
+          if (kM == 1) {
+            acc = fma_acc(v[j], xv[j], acc);
+          } else {
+            A *q = buf + (c[j] & mask) * kM + slot;
+            *q = fma_acc(v[j], xv[j], *q);
+            __syncwarp();
+          }
+        }
+    }
+    A *out = part + u * height;
+    if (kM == 1) {
+      if (lane < height) out[lane] = acc;
+    } else {
+      __syncwarp();
+      const int r = lane / G, pt = lane - r * G;
+      A sum = A(0);
+      if (r < height) {
+        A *q = buf + r * kM + pt * per;
+        sum = q[0];
+        q[0] = A(0);
+        for (int m = 1; m < per; ++m) {
+          sum += q[m];
+          q[m] = A(0);
+        }
+      }
+      for (int o = G >> 1; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (pt == 0 && r < height) out[r] = sum;
+      __syncwarp();
+    }
+  }
+}
+
+// y[row] = the P partial sums of the row, added in part order.
+template <typename A>
+__global__ void k_pad_combine(int rows, int height, int P, const A *__restrict__ part, A *__restrict__ y,
+                              const int32_t *__restrict__ row_map) {
+  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  const long long s = row / height, r = row - s * height;
+  const A *q = part + s * P * height + r;
+  A sum = q[0];
+  for (int p = 1; p < P; ++p) sum += q[(long long)p * height];
+  const long long t = row_map ? row_map[row] : row;
+  if (t >= 0 && t < rows) y[t] = sum;
+}
+
+// Parts per strip: 1 unless the strips are fewer than two per resident warp
+// (8 warps x 6 CTAs per SM, the plain walk's residency) and average at least
+// 64 passes; then enough parts for two units per resident warp, each of at
+// least 16 passes on average.
+int pad_parts(const cmrs_matrix *A) {
+  if (A->strips <= 0 || !(A->flags & CMRS_PADDED)) return 1;
+  const long long target = 2LL * sm_count() * kPadWarps * 6;
+  const long long avg = (long long)A->nnz / 32 / A->strips;
+  if ((long long)A->strips >= target || avg < 64) return 1;
+  long long P = ceil_div(target, A->strips);
+  P = std::min<long long>(P, avg / 16);
+  return (int)std::max<long long>(1, std::min<long long>(P, 4096));
+}
+
+// Workspace bytes of the split walk: the status word, then the partial sums.
+size_t pad_split_ws_bytes(const cmrs_matrix *A, int P) {
+  const size_t acc = A->dtype == CMRS_F64 ? 8 : 4;
+  return P > 1 ? 256 + align256((size_t)A->strips * P * A->height * acc) : 256;
+}
+
 // ============================================================== PADDED bulk-staged mapping
 // Bulk-staged walk for M = 1 (height 32).  One lane per warp copies the
 // warp's strips, kPadCh passes at a time, into a two-stage shared-memory ring
@@ -948,15 +1069,18 @@ struct Occ {
   int val[64] = {0};
 };
 
+// Resident CTAs per SM for `smem` bytes of dynamic shared memory, cached per
+// device.  The kernel is first opted in to max(smem, smem_cap) bytes, the most
+// any launch of it asks for.
 template <typename K>
-int occupancy(K kernel, int threads, size_t smem, Occ &cache) {
+int occupancy(K kernel, int threads, size_t smem, Occ &cache, size_t smem_cap = 0) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   std::lock_guard<std::mutex> lk(cache.mu);
   if (cache.val[dev] == 0) {
-    // opt in to the dynamic shared memory the launch uses (static + dynamic may pass 48 KB)
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // opt in to the dynamic shared memory the launches use (static + dynamic may pass 48 KB)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(smem, smem_cap));
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
     cache.val[dev] = n;
@@ -981,8 +1105,24 @@ size_t merge_ws_bytes(int nnz) {
 template <int DT, int kM>
 int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, const typename Form<DT>::Stored *lo,
                   const typename Form<DT>::Acc *x, typename Form<DT>::Acc *y, const int32_t *row_map,
-                  uint32_t *status, cudaStream_t st) {
+                  uint32_t *status, char *ws, size_t ws_bytes, cudaStream_t st) {
   typedef typename Form<DT>::Acc Acc;
+  const int P = pad_parts(A);
+  if (P > 1 && ws_bytes >= pad_split_ws_bytes(A, P)) {  // few long strips: several warps per strip
+    static Occ occ_split[33];
+    Acc *part = reinterpret_cast<Acc *>(ws + 256);
+    const size_t per_h = kM > 1 ? (size_t)kPadWarps * kM * sizeof(Acc) : 0;
+    const int per_sm = occupancy(k_spmv_padded_split<DT, kM>, kPadWarps * 32, per_h * A->height,
+                                 occ_split[A->height], per_h * 32);
+    const long long units = (long long)A->strips * P;
+    const int grid = (int)std::min<long long>(ceil_div(units, kPadWarps), (long long)per_sm * sm_count());
+    k_spmv_padded_split<DT, kM><<<grid, kPadWarps * 32, per_h * A->height, st>>>(
+        A->height, A->bits, A->strips, P, A->strip_ptr, A->col_packed, hi, lo, x, part);
+    CMRS_LAUNCH_CHECK();
+    k_pad_combine<Acc><<<(int)ceil_div(A->rows, 256), 256, 0, st>>>(A->rows, A->height, P, part, y, row_map);
+    CMRS_LAUNCH_CHECK();
+    return CMRS_OK;
+  }
   const bool aligned = ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(hi) |
                          reinterpret_cast<uintptr_t>(lo)) & 15) == 0;
   // short strips (a pass or a few) pay a copy round trip each: the plain walk is faster there
@@ -1011,7 +1151,7 @@ int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, con
 
 template <int DT>
 int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_map, int variant, char *ws,
-           cudaStream_t st) {
+           size_t ws_bytes, cudaStream_t st) {
   typedef typename Form<DT>::Stored S;
   typedef typename Form<DT>::Acc Acc;
   const S *hi = reinterpret_cast<const S *>(A->val);
@@ -1040,10 +1180,10 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
     CMRS_LAUNCH_CHECK();
   } else if (variant == CMRS_VARIANT_PADDED) {
     switch (CMRS_PAD_SLOTS_OF(A->flags)) {
-      case 1: return launch_padded<DT, 1>(A, hi, lo, x, y, row_map, status, st);
-      case 2: return launch_padded<DT, 2>(A, hi, lo, x, y, row_map, status, st);
-      case 4: return launch_padded<DT, 4>(A, hi, lo, x, y, row_map, status, st);
-      default: return launch_padded<DT, 8>(A, hi, lo, x, y, row_map, status, st);
+      case 1: return launch_padded<DT, 1>(A, hi, lo, x, y, row_map, status, ws, ws_bytes, st);
+      case 2: return launch_padded<DT, 2>(A, hi, lo, x, y, row_map, status, ws, ws_bytes, st);
+      case 4: return launch_padded<DT, 4>(A, hi, lo, x, y, row_map, status, ws, ws_bytes, st);
+      default: return launch_padded<DT, 8>(A, hi, lo, x, y, row_map, status, ws, ws_bytes, st);
     }
   } else {
     static Occ occ;
@@ -1131,7 +1271,9 @@ extern "C" int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *by
   int v = 0;
   rc = resolve_variant(A, variant, &v);
   if (rc) return rc;
-  *bytes = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz) : 256;
+  *bytes = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz)
+           : v == CMRS_VARIANT_PADDED ? pad_split_ws_bytes(A, pad_parts(A))
+                                       : 256;
   return CMRS_OK;
 }
 
@@ -1167,10 +1309,10 @@ int spmv_impl(const cmrs_matrix *A, const void *x, void *y, const int32_t *row_m
   }
   char *ws = reinterpret_cast<char *>(workspace);
   switch (A->dtype) {
-    case CMRS_F64: return launch<CMRS_F64>(A, x, y, row_map, v, ws, st);
-    case CMRS_F32: return launch<CMRS_F32>(A, x, y, row_map, v, ws, st);
-    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, row_map, v, ws, st);
-    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, row_map, v, ws, st);
+    case CMRS_F64: return launch<CMRS_F64>(A, x, y, row_map, v, ws, workspace_bytes, st);
+    case CMRS_F32: return launch<CMRS_F32>(A, x, y, row_map, v, ws, workspace_bytes, st);
+    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, row_map, v, ws, workspace_bytes, st);
+    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, row_map, v, ws, workspace_bytes, st);
   }
   return CMRS_ERR_ARG;
 }
@@ -1259,10 +1401,10 @@ extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, v
   CMRS_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, st));
   char *ws = reinterpret_cast<char *>(scratch);
   switch (A->dtype) {
-    case CMRS_F64: return launch<CMRS_F64>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
-    case CMRS_F32: return launch<CMRS_F32>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
-    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
-    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, st);
+    case CMRS_F64: return launch<CMRS_F64>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, sizeof(cmrs_noalloc_scratch), st);
+    case CMRS_F32: return launch<CMRS_F32>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, sizeof(cmrs_noalloc_scratch), st);
+    case CMRS_BF16: return launch<CMRS_BF16>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, sizeof(cmrs_noalloc_scratch), st);
+    case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, sizeof(cmrs_noalloc_scratch), st);
   }
   return CMRS_ERR_ARG;
 }

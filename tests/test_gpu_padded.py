@@ -158,6 +158,57 @@ def test_padded_short_strips(b, dtype):
     assert np.all(np.abs(y - yref) <= tol)
 
 
+def long_rows(seed, n=1000, cols=60000):
+    """Few long rows (1,500..2,500 entries): few strips of many passes, so
+    the padded product splits each strip over several warps; a ragged last
+    strip and some empty rows."""
+    L = np.random.default_rng(seed).integers(1500, 2500, n)
+    L[7:12] = 0
+    L[-3:] = 0
+    return inputs.from_lengths(L, cols, seed=seed + 30)
+
+
+@pytest.mark.parametrize("h,slots", HM)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_padded_split_strips(b, h, slots, dtype):
+    a = long_rows(dtype + h)
+    P = b.cmrs_pad(convert(b, a, h, dtype), slots)
+    ws = P.spmv_workspace(b.CMRS_VARIANT_PADDED)
+    assert ws.numel() > 256  # the workspace holds the partial sums of the split walk
+    x = xvec(a, dtype)
+    check_spmv(b, P, a, x, b.CMRS_VARIANT_PADDED, dtype)
+    y1 = b.cmrs_spmv(P, torch.from_numpy(x).cuda(), variant=b.CMRS_VARIANT_PADDED)
+    y2 = b.cmrs_spmv(P, torch.from_numpy(x).cuda(), variant=b.CMRS_VARIANT_PADDED)
+    assert torch.equal(y1, y2)  # partials are added in part order: the same result every call
+    # a workspace too small for the partial sums runs the one-warp-per-strip walk
+    small = b.workspace(256, "cuda")
+    y3 = b.cmrs_spmv(P, torch.from_numpy(x).cuda(), variant=b.CMRS_VARIANT_PADDED, workspace_tensor=small)
+    check_spmv_result(y3, a, x, dtype)
+
+
+def check_spmv_result(y, a, x, dtype):
+    y = y.cpu().numpy().astype(np.float64)
+    if dtype == 0:
+        yref, absy = orc.csr_spmv(a.row_ptr, a.col_ind, a.val.astype(np.float64), x)
+        assert np.all(np.abs(y - yref) <= 1e-12 * absy)
+    else:
+        vq = orc.decode(orc.encode(a.val, dtype), dtype, a.nnz)
+        yq, aq = orc.csr_spmv(a.row_ptr, a.col_ind, vq, x.astype(np.float64))
+        assert np.all(np.abs(y - yq) <= (np.diff(a.row_ptr) + 2) * 2.0**-24 * aq)
+
+
+def test_padded_split_with_row_map(b):
+    a = long_rows(5, n=1500)
+    rp = torch.from_numpy(a.row_ptr).cuda()
+    perm = b.cmrs_row_order(rp, 512)
+    rp2, ci2, v2 = b.cmrs_permute_csr(rp, torch.from_numpy(a.col_ind).cuda(), torch.from_numpy(a.val).cuda(), perm)
+    x = xvec(a, 0)
+    for h, slots in ((32, 1), (16, 8), (4, 8)):
+        Q = b.cmrs_pad(b.cmrs_from_csr(rp2, ci2, v2, a.cols, h), slots)
+        y = b.cmrs_spmv_rows(Q, torch.from_numpy(x).cuda(), perm)
+        check_spmv_result(y, a, x, 0)
+
+
 def test_padded_rejections(b):
     a = skewed(3, 2000)
     M = convert(b, a, 16)
