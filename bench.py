@@ -492,6 +492,7 @@ def run_ours(args):
         line["modified_cmrs"] = modified_cmrs(b, a, xd, rp, ci, va, flush, stream)
         line["heights_f64_row"] = height_sweep(b, a, xd, rp, ci, va, flush, stream)
         line["strip_sorted_vs_unsorted_f64"] = sorted_strips(b, a, xd, rp, ci, va, flush, stream)
+        line["selector"] = selector_cost(b, a, rp, ci)
         line["conversion"] = conversion_times(b, a, rp, ci, va, M_csr, h,
                                               args.slots if args.variant == "padded" else None)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -614,6 +615,25 @@ def variant_sweep(b, a, xd, M64, flush, stream, bp, steps=100):
         ms = statistics.mean(time_steps(lambda: b.cmrs_spmv(M64, xd, y, v, ws), steps, flush, stream))
         out[name] = {"ms": ms, "gbs": bp / (ms / 1e3) / 1e9}
     return out
+
+
+def selector_cost(b, a, rp, ci, reps=5):
+    """The strip selector on the headline matrix: the committed network
+    (features pass + forward + argmin, one read-back) and its choice, median
+    wall time of `reps` calls."""
+    import torch
+    from paper_1203_2946_gb300 import selector
+    model = selector.load_model(os.path.join(ROOT, "paper_1203_2946_gb300", "data", "selector_model.npz"))
+    ts, pick = [], None
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pick = b.cmrs_select_strip(rp, ci, a.cols, model)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    h, v, m = pick
+    name = ("h=%d/padded-m%d" % (h, m)) if v == b.CMRS_VARIANT_PADDED else "h=%d/%s" % (h, ("row", "strip", "merge")[v])
+    return {"ms": statistics.median(ts[1:]) * 1e3, "choice": name}
 
 
 def sorted_strips(b, a, xd, rp, ci, va, flush, stream, steps=60):
@@ -789,7 +809,9 @@ def run_secondary(args):
                       "kernel_variant": ("row", "strip", "merge", "padded")[ran], "bytes_per_step": bp,
                       "l2": L2_NOTE},
                      {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                      "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": kname},
+                      "peak_kind": peak_kind + " (hbm_gbs)", "kernel": kname,
+                      "traffic": traffic_record(kname, "%s_%s_h%d" % (args.workload, name, h) + (
+                          "_m%d" % args.slots if args.variant == "padded" else ""))},
                      {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(x.nbytes),
                       "d2h_bytes_per_step": int(a.rows * x.itemsize), "ms_per_step": e_ms},
                      steps * (3 if ran == 2 else 2 if split else 1), sampler.summary(), extra)
