@@ -154,3 +154,30 @@ def test_reorder_host_validation(L):
     m.rows, m.cols, m.nnz, m.height, m.strips, m.bits, m.dtype = 10, 10, 5, 4, 3, 4, 0
     m.strip_ptr = m.col_packed = m.val = 256
     assert L.cmrs_spmv_rows(ctypes.byref(m), p, p, None, -1, p, 1 << 20, None) == 1   # no row map
+
+
+def test_padded_split_workspace(L):
+    """cmrs_spmv_workspace for padded matrices: few strips of many passes get
+    room for per-part row sums past the 256-byte status block (the split
+    walk); many short strips, or plain CMRS, need the status block only.
+    Host only: the device pointers are never read."""
+    from paper_1203_2946_gb300 import binding as b
+
+    def ws(strips, passes, height=16, slots=8, dtype=0, flags=None):
+        m = b.cmrs_matrix()
+        m.rows, m.cols, m.height, m.strips = strips * height, 1000, height, strips
+        m.nnz, m.bits, m.dtype = strips * passes * 32, L.cmrs_bits_for_height(height), dtype
+        m.flags = (2 | ({1: 0, 2: 1, 4: 2, 8: 3}[slots] << 8)) if flags is None else flags
+        m.max_strip_nnz = -1
+        m.strip_ptr = m.col_packed = m.val = 256
+        n = ctypes.c_size_t()
+        assert L.cmrs_spmv_workspace(ctypes.byref(m), 3 if flags is None else 0, ctypes.byref(n)) == 0
+        return n.value
+
+    few_long = ws(strips=10, passes=4096)
+    assert few_long > 256 and (few_long - 256) % 256 == 0
+    assert few_long - 256 >= 10 * 2 * 16 * 8            # at least two parts of 16 FP64 row sums per strip
+    assert ws(strips=10, passes=4096, dtype=1) < few_long  # FP32 sums take half the room
+    assert ws(strips=10, passes=40) == 256                # short strips: one warp per strip
+    assert ws(strips=200000, passes=64) == 256            # more strips than two per resident warp
+    assert ws(strips=10, passes=4096, flags=0) == 256     # plain CMRS, ROW
