@@ -346,6 +346,11 @@ __global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int
 // RowInStrip); the 32 partial sums of every row are then halved five times
 // (l += l + 16, 8, 4, 2, 1) and lanes < height write the rows.  The buffer is
 // laid out row-major [r][32] so that the lanes of a warp touch 32 banks.
+// Each lane issues the loads of kStripU of its entries before their sums.
+#ifndef CMRS_STRIP_U
+#define CMRS_STRIP_U 4
+#endif
+constexpr int kStripU = CMRS_STRIP_U;
 template <int DT>
 __global__ void __launch_bounds__(kStripWarps * 32) k_spmv_strip(int rows, int height, int bits, int strips,
                                                                   const int32_t *__restrict__ sp,
@@ -365,12 +370,29 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_spmv_strip(int rows, int h
   for (int s = blockIdx.x * kStripWarps + w; s < strips; s += nw) {
     for (int r = 0; r < height; ++r) buf[r * 32 + lane] = A(0);
     const int a = sp[s], b = sp[s + 1];
-    for (int j = a + lane; j < b; j += 32) {
-      const uint32_t c = packed[j];
-      const int r = (int)(c & mask);
-      if (r < height) {
-        A *p = buf + r * 32 + lane;
-        *p = fma_acc(Form<DT>::value(hi, vl, j), ld_x(x + (c >> bits)), *p);
+    for (int j0 = a; j0 < b; j0 += 32 * kStripU) {  // kStripU steps' loads in flight
+      uint32_t c[kStripU];
+      A v[kStripU], xv[kStripU];
+#pragma unroll
+      for (int u = 0; u < kStripU; ++u) {
+        const int j = j0 + 32 * u + lane;
+        if (j < b) {
+          c[u] = packed[j];
+          v[u] = Form<DT>::value(hi, vl, j);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kStripU; ++u)
+        if (j0 + 32 * u + lane < b) xv[u] = ld_x(x + (c[u] >> bits));
+#pragma unroll
+      for (int u = 0; u < kStripU; ++u) {
+        if (j0 + 32 * u + lane < b) {
+          const int r = (int)(c[u] & mask);
+          if (r < height) {
+            A *p = buf + r * 32 + lane;
+            *p = fma_acc(v[u], xv[u], *p);
+          }
+        }
       }
     }
     __syncwarp();
