@@ -450,7 +450,7 @@ __device__ __forceinline__ typename Form<DT>::Acc ld_val_stream(const typename F
   }
 }
 
-template <int DT, int kM>
+template <int DT, int kM, bool kExact>
 __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(int rows, int height, int bits, int strips,
                                                                const int32_t *__restrict__ sp,
                                                                const uint32_t *__restrict__ packed,
@@ -478,22 +478,24 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
       __syncwarp();
     }
     const int a = sp[s], b = sp[s + 1];  // multiples of 32
-    for (int k0 = a; k0 < b; k0 += 32 * kPadU) {
-      uint32_t c[kPadU];
-      A v[kPadU], xv[kPadU];
-#pragma unroll
-      for (int u = 0; u < kPadU; ++u)
-        if (k0 + 32 * u < b) {  // warp-uniform
+    if constexpr (kExact) {
+      // NU passes from k0, every one present: no guard that the compiler could
+      // turn into a multiply-add computed and then discarded (on this GPU an
+      // FP64 warp instruction costs its issue slot whatever its lanes do)
+      auto group = [&](auto nu, int k0) {
+        constexpr int NU = decltype(nu)::value;
+        uint32_t c[NU];
+        A v[NU], xv[NU];
+  #pragma unroll
+        for (int u = 0; u < NU; ++u) {
           const long long k = (long long)k0 + 32 * u + lane;
           c[u] = ld_stream(packed + k, pol);
           v[u] = ld_val_stream<DT>(hi, lo, k, pol);
         }
-#pragma unroll
-      for (int u = 0; u < kPadU; ++u)
-        if (k0 + 32 * u < b) xv[u] = ld_x(x + (c[u] >> bits));
-#pragma unroll
-      for (int u = 0; u < kPadU; ++u)
-        if (k0 + 32 * u < b) {
+  #pragma unroll
+        for (int u = 0; u < NU; ++u) xv[u] = ld_x(x + (c[u] >> bits));
+  #pragma unroll
+        for (int u = 0; u < NU; ++u) {
           if (kM == 1) {
             acc = fma_acc(v[u], xv[u], acc);
           } else {
@@ -502,6 +504,37 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
             __syncwarp();
           }
         }
+      };
+      int k0 = a;
+      for (; k0 + 32 * kPadU <= b; k0 += 32 * kPadU) group(std::integral_constant<int, kPadU>(), k0);
+      for (; k0 + 64 <= b; k0 += 64) group(std::integral_constant<int, 2>(), k0);  // the last passes: twos,
+      if (k0 < b) group(std::integral_constant<int, 1>(), k0);                         // then one
+    } else {  // groups of kPadU passes, the strip's last group guarded
+      for (int k0 = a; k0 < b; k0 += 32 * kPadU) {
+        uint32_t c[kPadU];
+        A v[kPadU], xv[kPadU];
+  #pragma unroll
+        for (int u = 0; u < kPadU; ++u)
+          if (k0 + 32 * u < b) {  // warp-uniform
+            const long long k = (long long)k0 + 32 * u + lane;
+            c[u] = ld_stream(packed + k, pol);
+            v[u] = ld_val_stream<DT>(hi, lo, k, pol);
+          }
+  #pragma unroll
+        for (int u = 0; u < kPadU; ++u)
+          if (k0 + 32 * u < b) xv[u] = ld_x(x + (c[u] >> bits));
+  #pragma unroll
+        for (int u = 0; u < kPadU; ++u)
+          if (k0 + 32 * u < b) {
+            if (kM == 1) {
+              acc = fma_acc(v[u], xv[u], acc);
+            } else {
+              A *p = buf + (c[u] & mask) * kM + slot;
+              *p = fma_acc(v[u], xv[u], *p);
+              __syncwarp();
+            }
+          }
+      }
     }
     const long long row0 = (long long)s * height;
     if (kM == 1) {
@@ -1160,13 +1193,23 @@ int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, con
     CMRS_LAUNCH_CHECK();
     return CMRS_OK;
   }
-  static Occ occ;
+  // Groups of exactly present passes (no guarded multiply-add that the compiler
+  // computes and discards) pay off for strips of under 4 passes on average and
+  // for FP64 slot buffers; long one-slot strips keep the guarded last group.
+  const bool exact = (long long)A->nnz < 4LL * 32 * A->strips || (DT == CMRS_F64 && kM > 1);
+  static Occ occ[2];
   const size_t smem = (size_t)kPadWarps * kM * A->height * sizeof(Acc);
-  const int per_sm = occupancy(k_spmv_padded<DT, kM>, kPadWarps * 32, (size_t)kPadWarps * kM * 32 * sizeof(Acc), occ);
+  const size_t smem_occ = (size_t)kPadWarps * kM * 32 * sizeof(Acc);
+  const int per_sm = exact ? occupancy(k_spmv_padded<DT, kM, true>, kPadWarps * 32, smem_occ, occ[1])
+                           : occupancy(k_spmv_padded<DT, kM, false>, kPadWarps * 32, smem_occ, occ[0]);
   const long long need = ceil_div(A->strips, kPadWarps);
   const int grid = (int)std::min<long long>(need, (long long)per_sm * sm_count());
-  k_spmv_padded<DT, kM><<<grid, kPadWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->strip_ptr,
-                                                             A->col_packed, hi, lo, x, y, row_map);
+  if (exact)
+    k_spmv_padded<DT, kM, true><<<grid, kPadWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips,
+                                                                    A->strip_ptr, A->col_packed, hi, lo, x, y, row_map);
+  else
+    k_spmv_padded<DT, kM, false><<<grid, kPadWarps * 32, smem, st>>>(A->rows, A->height, A->bits, A->strips,
+                                                                     A->strip_ptr, A->col_packed, hi, lo, x, y, row_map);
   CMRS_LAUNCH_CHECK();
   return CMRS_OK;
 }
