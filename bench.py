@@ -219,6 +219,54 @@ def run_reference(args):
         a = inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind, a.val.astype(np.float64))
         x = x.astype(np.float64)
         wl = "power-law rows n=4194304, FP32 values widened to FP64, CRS order"
+    elif args.workload == "p7":
+        a = inputs.permutation_matrix()
+        x = inputs.uniform_vector(a.cols, 0)
+        wl = "p7: 10^7 x 10^7 random permutation, FP64, CRS order"
+    elif args.workload == "dense4":
+        a = inputs.dense_as_sparse()
+        x = inputs.uniform_vector(a.cols, 0)
+        wl = "dense4: 10^4 x 10^4 dense matrix stored as sparse, FP64, CRS order"
+    elif args.workload == "irregular":
+        a, x = inputs.workload_irregular()
+        wl = "banded rows of 4..60 entries, n=2097152, FP64, CRS order"
+    elif args.workload == "batched":
+        # a bounded sample of the batch: the first 8 matrices, one CRS product per right-hand side
+        specs = inputs.batched_banded_specs()[:8]
+        mats = []
+        for sp in specs:  # FP64 copies, X by column, made before any timing
+            a, X = inputs.batched_banded(sp)
+            mats.append((a, np.ascontiguousarray(a.val, dtype=np.float64), np.ascontiguousarray(X.T, dtype=np.float64)))
+        lib = oracle.lib()
+        ts, bytes_ = [], []
+        t_end = time.perf_counter() + 60.0
+        for i in range(args.steps + args.warmup):
+            a, vd, XT = mats[i % len(mats)]
+            k = XT.shape[0]
+            y = np.empty(a.rows)
+            t0 = time.perf_counter()
+            for c in range(k):
+                lib.orc_csr_spmv(a.rows, oracle._p(a.row_ptr), oracle._p(a.col_ind), oracle._p(vd), oracle._p(XT[c]),
+                                 oracle._p(y), None)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                ts.append(dt)
+                S = (a.rows + args.height - 1) // args.height
+                bytes_.append((4 + 4) * a.nnz + 4 * S + 4 * k * (a.rows + a.cols))  # the GPU line's beta+, FP32
+            if time.perf_counter() > t_end and len(ts) >= 1:
+                break
+        value = sum(bytes_) / sum(ts) / 1e9
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+                "steps": len(ts), "warmup": args.warmup, "ms_per_step": sum(ts) / len(ts) * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "batched banded-random SpMM, the first %d of the 256 matrices in turn, one "
+                                       "CRS product per right-hand side (FP32 values and X widened to FP64)" % len(mats)},
+                "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                 "sample": "one matrix with all its right-hand sides per step, %d steps" % len(ts)},
+                "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     else:
         a, x = inputs.workload_laplacian_64()
         wl = "5-point Laplacian 64x64, FP64, CRS order"
