@@ -96,14 +96,20 @@ __device__ bool pad_strip_fill(int sa, int sb, int height, int bits, int slots, 
     if (wanted <= room) {
       extra = max(want, 0);  // every row gets what it wants
     } else {
-      const unsigned long long key =
-          want > 0 ? ((unsigned long long)(left - take) << 6) | (unsigned long long)(63 - lane) : 0ull;
-      int before = 0;
-      for (unsigned m = __ballot_sync(kFull, want > 0); m; m &= m - 1) {
-        const int j = __ffs(m) - 1;
-        const unsigned long long kj = __shfl_sync(kFull, key, j);
-        const int wj = __shfl_sync(kFull, want, j);
-        if (kj > key) before += wj;
+      // before = the want of the rows ranked ahead (more items left, or as
+      // many and a lower row), one distinct count of items left at a time,
+      // largest first, until the free room is given out
+      const int lv = want > 0 ? left - take : 0;  // >= 1 for a row that wants
+      unsigned rem = __ballot_sync(kFull, want > 0);
+      int before = room, done = 0;
+      while (rem && done < room) {
+        const int v = (int)__reduce_max_sync(kFull, (rem >> lane) & 1u ? (unsigned)lv : 0u);
+        const unsigned g = __ballot_sync(kFull, ((rem >> lane) & 1u) && lv == v);
+        const int wg = (g >> lane) & 1u ? want : 0;
+        const int below = warp_excl_scan(wg, lane);  // want of the group's lower rows
+        if ((g >> lane) & 1u) before = done + below;
+        done += (int)__reduce_add_sync(kFull, (unsigned)wg);
+        rem &= ~g;
       }
       extra = want > 0 ? max(0, min(want, room - before)) : 0;
     }
@@ -198,7 +204,7 @@ __device__ bool pad_strip_fill_m1(int sa, int sb, int bits, long long limit, con
 }
 
 template <typename S, bool kSplit>
-__global__ void __launch_bounds__(kPadWarps * 32) k_pad_fill(int strips, int height, int bits, int slots,
+__global__ void __launch_bounds__(kPadWarps * 32, 4) k_pad_fill(int strips, int height, int bits, int slots,
                                                             const int32_t *__restrict__ sp,
                                                             const uint32_t *__restrict__ packed,
                                                             const S *__restrict__ vh, const S *__restrict__ vl,
