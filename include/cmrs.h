@@ -95,7 +95,11 @@ extern "C" {
  *                       shared buffer, the slots of each row are summed at
  *                       the strip's end (M = 1: lane r keeps row r's sum in a
  *                       register, no buffer).  Fully coalesced 32-bit loads,
- *                       no search for row starts.
+ *                       no search for row starts.  The FP32 and BF16 forms at
+ *                       M = 1 with long strips stream them through a
+ *                       shared-memory ring of bulk copies; few long strips
+ *                       are split over several warps (see
+ *                       cmrs_spmv_workspace).
  *   CMRS_VARIANT_AUTO   (-1) PADDED for padded strips, STRIP for sorted
  *                       strips.  Otherwise, with
  *                       mu = nnz / rows: MERGE if mu < 2, mu > 32, or
