@@ -205,6 +205,44 @@ def cpu_oracle_rate(a, x, strips, budget_s=12.0, max_reps=200):
             "ms_per_spmv": t * 1e3, "gflops": 2 * a.nnz / t / 1e9}
 
 
+def cpu_oracle_rate_all_cores(a, x, strips, runs=11):
+    """The same oracle on every core this process may use: the rows split into
+    one contiguous slice per core, each slice's plain C loop called from its own
+    Python thread (the call releases the interpreter lock), so every row's sum
+    is the single-thread oracle's.  11 runs, the slowest dropped, the mean of
+    the other 10.  A reported baseline only."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cores = max(1, len(os.sched_getaffinity(0)))
+    lib = oracle.lib()
+    rp = np.ascontiguousarray(a.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(a.col_ind, dtype=np.int32)
+    va = np.ascontiguousarray(a.val, dtype=np.float64)
+    xv = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(a.rows)
+    cuts = [a.rows * i // cores for i in range(cores + 1)]
+    parts = [(cuts[i], cuts[i + 1]) for i in range(cores) if cuts[i + 1] > cuts[i]]
+
+    def one(r):
+        r0, r1 = r
+        lib.orc_csr_spmv(r1 - r0, oracle._p(rp[r0:]), oracle._p(ci), oracle._p(va), oracle._p(xv),
+                         oracle._p(y[r0:]), None)
+
+    ts = []
+    with ThreadPoolExecutor(len(parts)) as pool:
+        list(pool.map(one, parts))  # warm-up
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            list(pool.map(one, parts))
+            ts.append(time.perf_counter() - t0)
+    ref = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val, x)
+    same = bool(np.array_equal(y, ref[0] if isinstance(ref, tuple) else ref))
+    t = statistics.mean(sorted(ts)[:-1])
+    return {"value": beta_plus(a.nnz, a.rows, strips, 8) / t / 1e9, "unit": "GB/s", "cores": len(parts),
+            "kind": "oracle, rows split over threads", "sample": "full matrix, %d runs, slowest dropped" % runs,
+            "ms_per_spmv": t * 1e3, "same_y_as_single_thread": same}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -545,6 +583,7 @@ def run_ours(args):
                                               args.slots if args.variant == "padded" else None)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(a, x, strips)
+        line["cpu_baseline_all_cores"] = cpu_oracle_rate_all_cores(a, x, strips)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
