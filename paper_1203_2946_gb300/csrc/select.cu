@@ -33,56 +33,137 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
-// One warp per row: row length statistics, |col - row| statistics and the
-// row's min/max column (for the strip spreads).
-__global__ void k_feat_rows(int rows, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                            int32_t *__restrict__ rmin, int32_t *__restrict__ rmax, FeatAcc *acc) {
-  __shared__ unsigned long long s[15];
+// Row length statistics, |col - row| statistics and each row's min/max
+// column (for the strip spreads).  A warp takes 32 consecutive rows at a
+// time: lane r holds row r's bounds and length statistics; the rows' entries
+// are one contiguous range, read in coalesced batches of 32 (kFeatU in
+// flight per lane); an entry finds its row among the 32 row starts by a
+// five-step shuffle search, adds its |col - row| to sums over all entries,
+// and a segmented shuffle scan over the batch gives each row's min and max,
+// which the row's lane carries over batches.  The strips of every height
+// h = 2^e <= 32 are aligned groups of h lanes, so a shuffle tree over the
+// rows' min and max gives each strip's column spread in the same pass.  A
+// group with an invalid RowPtr range is skipped.
+constexpr int kFeatU = 4;
+__global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            FeatAcc *acc) {
+  __shared__ unsigned long long s[15], s_spread[6], s_ne[6];
   if (threadIdx.x < 15) s[threadIdx.x] = 0;
+  if (threadIdx.x < 6) {
+    s_spread[threadIdx.x] = 0;
+    s_ne[threadIdx.x] = 0;
+  }
   __syncthreads();
+  const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long groups = ((long long)rows + 31) / 32;
   unsigned long long l2 = 0, mxl = 0, empty = 0, same = 0, near = 0, sd = 0, mxd = 0;
   unsigned long long bins[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += nw) {
-    const int a = rp[i], b = rp[i + 1];
-    unsigned long long d_sum = 0, d_max = 0, d_near = 0;
-    int lo = INT32_MAX, hi = -1;
-    for (int k = a + lane; k < b; k += 32) {
-      const int c = ci[k];
-      const long long d = (long long)c - i;
-      const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
-      d_sum += ad;
-      d_max = max(d_max, ad);
-      d_near += ad <= 64 ? 1ull : 0ull;
-      lo = min(lo, c);
-      hi = max(hi, c);
-    }
-    d_sum = warp_sum(d_sum);
-    d_max = warp_max(d_max);
-    d_near = warp_sum(d_near);
-    for (int o = 16; o > 0; o >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if (lane == 0) {
-      const unsigned long long l = (unsigned long long)(b - a);
+  for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups; g += nw) {
+    const long long r0 = g * 32, r = r0 + lane;
+    const int nrows = (int)min(32LL, (long long)rows - r0);
+    const int start = r < rows ? rp[r] : 0;
+    const int last = rp[min(r0 + 32, (long long)rows)];
+    int end = __shfl_down_sync(kAll, start, 1);
+    if (lane == 31 || r + 1 >= rows) end = last;
+    const bool ok = lane >= nrows || (start >= 0 && end >= start && end <= nnz);
+    if (!__all_sync(kAll, ok)) continue;
+    // row lengths (lane r)
+    const int len = end - start;
+    int lprev = __shfl_up_sync(kAll, len, 1);
+    if (lane == 0) lprev = r0 > 0 ? start - rp[r0 - 1] : -1;
+    if (lane < nrows) {
+      const unsigned long long l = (unsigned long long)len;
       l2 += l * l;
       mxl = max(mxl, l);
       empty += l == 0;
-      if (i > 0 && l == (unsigned long long)(a - rp[i - 1])) same++;
+      if (r > 0 && len == lprev) same++;
       if (l >= 1) {
         int bb = 0;
         while (bb < 7 && l >= (2ull << bb)) ++bb;
-        bins[bb]++;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) bins[q] += q == bb;  // registers, not a local array
       }
-      sd += d_sum;
-      mxd = max(mxd, d_max);
-      near += d_near;
-      rmin[i] = lo;
-      rmax[i] = hi;
+    }
+    // entries
+    const int key = lane < nrows ? start : last;  // rows past the matrix sort last
+    const int e0 = __shfl_sync(kAll, start, 0);
+    int lo = INT32_MAX, hi = -1;  // row `lane`'s min and max column
+    for (int k0 = e0; k0 < last; k0 += 32 * kFeatU) {
+      int c[kFeatU];
+#pragma unroll
+      for (int u = 0; u < kFeatU; ++u) {
+        const int k = k0 + 32 * u + lane;
+        c[u] = k < last ? ci[k] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kFeatU; ++u) {
+        const int kb = k0 + 32 * u;  // first entry of this batch
+        if (kb >= last) break;       // warp-uniform
+        const int k = kb + lane;
+        const bool valid = k < last;
+        int j = 0;  // row of entry k: the last of the group's rows starting at or before k
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int sj = __shfl_sync(kAll, key, j + step);
+          if (sj <= k) j += step;
+        }
+        if (valid) {
+          const long long d = (long long)c[u] - (r0 + j);
+          const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+          sd += ad;
+          mxd = max(mxd, ad);
+          near += ad <= 64 ? 1ull : 0ull;
+        }
+        // min / max over the lanes of the same row in this batch
+        const int seg = max(__shfl_sync(kAll, key, j), kb) - kb;  // first lane of row j in the batch
+        int vmin = valid ? c[u] : INT32_MAX, vmax = valid ? c[u] : -1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int tmin = __shfl_up_sync(kAll, vmin, o), tmax = __shfl_up_sync(kAll, vmax, o);
+          if (lane - o >= seg) {
+            vmin = min(vmin, tmin);
+            vmax = max(vmax, tmax);
+          }
+        }
+        // row `lane` takes the scan at its last entry in the batch
+        const int my_e = min(end, kb + 32) - kb - 1;
+        const bool mine = lane < nrows && max(start, kb) - kb <= my_e;
+        const int m1 = __shfl_sync(kAll, vmin, mine ? my_e : 0), m2 = __shfl_sync(kAll, vmax, mine ? my_e : 0);
+        if (mine) {
+          lo = min(lo, m1);
+          hi = max(hi, m2);
+        }
+      }
+    }
+    // strip spreads: after step e each lane holds the min and max of its
+    // aligned group of 2^e rows (rows past the matrix, and empty rows, are
+    // neutral); the group's first lane counts the strip if it has entries
+    int slo = lane < nrows ? lo : INT32_MAX, shi = lane < nrows ? hi : -1;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      if (e > 0) {
+        slo = min(slo, __shfl_xor_sync(kAll, slo, 1 << (e - 1)));
+        shi = max(shi, __shfl_xor_sync(kAll, shi, 1 << (e - 1)));
+      }
+      const bool counted = (lane & ((1 << e) - 1)) == 0 && shi >= 0;
+      const unsigned long long sp = warp_sum(counted ? (unsigned long long)(shi - slo) : 0ull);
+      const unsigned long long ne = warp_sum(counted ? 1ull : 0ull);
+      if (lane == 0 && ne) {
+        atomicAdd(&s_spread[e], sp);
+        atomicAdd(&s_ne[e], ne);
+      }
     }
   }
+  l2 = warp_sum(l2);
+  mxl = warp_max(mxl);
+  empty = warp_sum(empty);
+  same = warp_sum(same);
+  near = warp_sum(near);
+  sd = warp_sum(sd);
+  mxd = warp_max(mxd);
+  for (int bb = 0; bb < 8; ++bb) bins[bb] = warp_sum(bins[bb]);
   if (lane == 0) {
     atomicAdd(&s[0], l2);
     atomicMax(&s[1], mxl);
@@ -104,71 +185,50 @@ __global__ void k_feat_rows(int rows, const int32_t *__restrict__ rp, const int3
     atomicMax(&acc->max_d, s[6]);
     for (int bb = 0; bb < 8; ++bb) atomicAdd(&acc->bins[bb], s[7 + bb]);
   }
-}
-
-// blockIdx.y = height index e (h = 2^e): spread of strip s = max - min column
-// over its rows, summed over non-empty strips.
-__global__ void k_feat_strips(int rows, const int32_t *__restrict__ rmin, const int32_t *__restrict__ rmax,
-                              FeatAcc *acc) {
-  __shared__ unsigned long long s_spread, s_nonempty;
-  if (threadIdx.x == 0) {
-    s_spread = 0;
-    s_nonempty = 0;
-  }
-  __syncthreads();
-  const int e = blockIdx.y;
-  const int h = 1 << e;
-  const long long strips = (rows + (long long)h - 1) / h;
-  unsigned long long sp = 0, ne = 0;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < strips;
-       s += (long long)gridDim.x * blockDim.x) {
-    int lo = INT32_MAX, hi = -1;
-    const long long r1 = min((s + 1) * h, (long long)rows);
-    for (long long r = s * h; r < r1; ++r) {
-      lo = min(lo, rmin[r]);
-      hi = max(hi, rmax[r]);
-    }
-    if (hi >= 0) {
-      sp += (unsigned long long)(hi - lo);
-      ne++;
-    }
-  }
-  sp = warp_sum(sp);
-  ne = warp_sum(ne);
-  if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&s_spread, sp);
-    atomicAdd(&s_nonempty, ne);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicAdd(&acc->spread[e], s_spread);
-    atomicAdd(&acc->nonempty[e], s_nonempty);
+  if (threadIdx.x < 6) {
+    atomicAdd(&acc->spread[threadIdx.x], s_spread[threadIdx.x]);
+    atomicAdd(&acc->nonempty[threadIdx.x], s_ne[threadIdx.x]);
   }
 }
 
 // The 24 features from the integer sums, with the same operations, in the
-// same order, as their definition (no contraction into FMAs).
+// same order, as their definition (no contraction into FMAs); thread t
+// computes feature t.
 __global__ void k_feat_final(int rows, int nnz, const FeatAcc *acc, double *f) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int t = threadIdx.x;
+  if (blockIdx.x != 0 || t >= kNFeat) return;
   const double n = (double)rows, z = (double)nnz;
   const double mu = __ddiv_rn(z, n);
-  double var = __dsub_rn(__ddiv_rn((double)acc->sum_l2, n), __dmul_rn(mu, mu));
-  if (var < 0.0) var = 0.0;
-  f[0] = log2(n);
-  f[1] = log2(z > 1.0 ? z : 1.0);
-  f[2] = log2(__dadd_rn(1.0, mu));
-  f[3] = __ddiv_rn(sqrt(var), mu > 1.0 ? mu : 1.0);
-  f[4] = log2(__dadd_rn(1.0, (double)acc->max_l));
-  f[5] = __ddiv_rn((double)acc->empty, n);
-  for (int b = 0; b < 8; ++b) f[6 + b] = __ddiv_rn((double)acc->bins[b], n);
-  f[14] = log2(__dadd_rn(1.0, nnz > 0 ? __ddiv_rn((double)acc->sum_d, z) : 0.0));
-  f[15] = log2(__dadd_rn(1.0, (double)acc->max_d));
-  f[16] = nnz > 0 ? __ddiv_rn((double)acc->near, z) : 0.0;
-  f[17] = rows > 1 ? __ddiv_rn((double)acc->same, (double)(rows - 1)) : 0.0;
-  for (int e = 0; e < 6; ++e) {
-    const double ne = (double)acc->nonempty[e];
-    f[18 + e] = log2(__dadd_rn(1.0, ne > 0 ? __ddiv_rn((double)acc->spread[e], ne) : 0.0));
+  double v;
+  if (t == 0) {
+    v = log2(n);
+  } else if (t == 1) {
+    v = log2(z > 1.0 ? z : 1.0);
+  } else if (t == 2) {
+    v = log2(__dadd_rn(1.0, mu));
+  } else if (t == 3) {
+    double var = __dsub_rn(__ddiv_rn((double)acc->sum_l2, n), __dmul_rn(mu, mu));
+    if (var < 0.0) var = 0.0;
+    v = __ddiv_rn(sqrt(var), mu > 1.0 ? mu : 1.0);
+  } else if (t == 4) {
+    v = log2(__dadd_rn(1.0, (double)acc->max_l));
+  } else if (t == 5) {
+    v = __ddiv_rn((double)acc->empty, n);
+  } else if (t < 14) {
+    v = __ddiv_rn((double)acc->bins[t - 6], n);
+  } else if (t == 14) {
+    v = log2(__dadd_rn(1.0, nnz > 0 ? __ddiv_rn((double)acc->sum_d, z) : 0.0));
+  } else if (t == 15) {
+    v = log2(__dadd_rn(1.0, (double)acc->max_d));
+  } else if (t == 16) {
+    v = nnz > 0 ? __ddiv_rn((double)acc->near, z) : 0.0;
+  } else if (t == 17) {
+    v = rows > 1 ? __ddiv_rn((double)acc->same, (double)(rows - 1)) : 0.0;
+  } else {
+    const double ne = (double)acc->nonempty[t - 18];
+    v = log2(__dadd_rn(1.0, ne > 0 ? __ddiv_rn((double)acc->spread[t - 18], ne) : 0.0));
   }
+  f[t] = v;
 }
 
 // ------------------------------------------------------------------ MLP (FP32)
@@ -266,7 +326,10 @@ size_t param_count(int nin, int nh, int nout) {
   return (size_t)nh * nin + nh + (size_t)nh * nh + nh + (size_t)nout * nh + nout;
 }
 
-size_t features_ws(int rows) { return align256(sizeof(FeatAcc)) + 2 * align256((size_t)std::max(rows, 1) * 4); }
+size_t features_ws(int rows) {
+  (void)rows;
+  return align256(sizeof(FeatAcc));
+}
 
 }  // namespace
 }  // namespace cmrs
@@ -287,15 +350,10 @@ extern "C" int cmrs_features(int rows, int nnz, const int32_t *row_ptr, const in
   cudaStream_t st = as_stream(stream);
   char *ws = reinterpret_cast<char *>(workspace);
   FeatAcc *acc = reinterpret_cast<FeatAcc *>(ws);
-  int32_t *rmin = reinterpret_cast<int32_t *>(ws + align256(sizeof(FeatAcc)));
-  int32_t *rmax = reinterpret_cast<int32_t *>(ws + align256(sizeof(FeatAcc)) + align256((size_t)rows * 4));
   CMRS_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(FeatAcc), st));
   const int sms = sm_count();
-  const int g = (int)std::min<long long>(ceil_div((long long)rows * 32, 256), (long long)sms * 8);
-  k_feat_rows<<<g, 256, 0, st>>>(rows, row_ptr, col_ind, rmin, rmax, acc);
-  CMRS_LAUNCH_CHECK();
-  dim3 g2((unsigned)std::min<long long>(ceil_div(rows, 256), (long long)sms * 4), 6);
-  k_feat_strips<<<g2, 256, 0, st>>>(rows, rmin, rmax, acc);
+  const int g = (int)std::min<long long>(ceil_div((long long)rows, 256), (long long)sms * 8);  // 8 warps x 32 rows
+  k_feat_rows<<<g, 256, 0, st>>>(rows, nnz, row_ptr, col_ind, acc);
   CMRS_LAUNCH_CHECK();
   k_feat_final<<<1, 32, 0, st>>>(rows, nnz, acc, feat);
   CMRS_LAUNCH_CHECK();
