@@ -308,6 +308,18 @@ int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, void *stream
  * else CMRS_OK.  Reads device memory synchronously on `stream`. */
 int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, void *stream);
 
+/* Diagnostic, not in the paper: exercises the timeout report of the staged
+ * kernels without a fault.  One warp waits, with the bounded mbarrier wait
+ * those kernels use for their bulk copies, on a phase that only an arrival of
+ * its own completes; arrive != 0 makes that arrival first, arrive == 0 leaves
+ * the phase open, so every lane gives up after `tries` tries (1..65536) and
+ * the kernel sets the timeout bit of the status word at the start of
+ * `workspace` (device, caller-owned, >= 256 bytes, 256-byte aligned) and
+ * returns.  cmrs_spmv_check on that workspace then reports CMRS_ERR_TIMEOUT
+ * and clears the bit.  No copy is issued, so none is left in flight.
+ * CMRS_ERR_ARG for a bad workspace or `tries`.  Asynchronous on `stream`. */
+int cmrs_wait_probe(void *workspace, uint32_t tries, int arrive, void *stream);
+
 /* ---- multi right-hand-side SpMM, single and batched ----------------------
  * Y = A X for CMRS_F32 matrices with unsorted strips; X device [cols][k] and
  * Y device [rows][k], row-major FP32, FP32 accumulation.  Not in the paper:

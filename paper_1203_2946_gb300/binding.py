@@ -87,6 +87,7 @@ def lib():
             "cmrs_pad_fill": ([M, i, vp, ctypes.c_int32, vp, vp, vp, M], i),
             "cmrs_spmv": ([M, vp, vp, i, vp, sz, vp], i),
             "cmrs_spmv_check": ([M, i, vp, vp], i),
+            "cmrs_wait_probe": ([vp, u, i, vp], i),
             "cmrs_spmv_noalloc": ([M, vp, vp, vp], i),
             "cmrs_spmm": ([M, i, vp, vp, vp], i),
             "cmrs_spmm_plan_workspace": ([i, vp, vp, i, ctypes.POINTER(sz)], i),
@@ -305,6 +306,12 @@ def cmrs_spmv_noalloc(A: Matrix, x, y=None, stream=None):
 def cmrs_spmv_check(A: Matrix, variant=CMRS_VARIANT_AUTO, stream=None):
     ws = A.spmv_workspace(variant)
     _check(lib().cmrs_spmv_check(A.ref(), variant, _ptr(ws), _stream(stream)), "cmrs_spmv_check")
+
+
+def cmrs_wait_probe(ws, tries, arrive, stream=None):
+    """Bounded in-kernel wait on a phase that completes only if `arrive`;
+    leaves the timeout bit in the status word of `ws` when it gives up."""
+    _check(lib().cmrs_wait_probe(_ptr(ws), int(tries), int(bool(arrive)), _stream(stream)), "cmrs_wait_probe")
 
 
 def cmrs_to_csr(A: Matrix, with_values=True, stream=None):

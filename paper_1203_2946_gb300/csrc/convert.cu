@@ -660,6 +660,7 @@ extern "C" int cmrs_from_csr(int rows, int cols, int nnz, const int32_t *row_ptr
                              const void *val_in, int val_in_dtype, int height, uint32_t flags, int dtype,
                              int32_t *strip_ptr_out, uint32_t *col_packed_out, void *val_out, void *workspace,
                              size_t workspace_bytes, void *stream, cmrs_matrix *out) {
+  CMRS_TRACE();
   if (rows < 0 || cols < 0 || nnz < 0) return CMRS_ERR_ARG;
   if (dtype < CMRS_F64 || dtype > CMRS_BF16X2) return CMRS_ERR_ARG;
   if (val_in_dtype != CMRS_F64 && val_in_dtype != CMRS_F32) return CMRS_ERR_ARG;
@@ -719,6 +720,7 @@ void launch_to_csr(bool sorted, int g, cudaStream_t st, const cmrs_matrix *A, co
 
 extern "C" int cmrs_to_csr(const cmrs_matrix *A, int32_t *row_ptr_out, int32_t *col_ind_out, void *val_out,
                            void *workspace, size_t workspace_bytes, void *stream) {
+  CMRS_TRACE();
   if (!A || !row_ptr_out || A->rows < 0 || A->nnz < 0) return CMRS_ERR_ARG;
   if (cmrs_bits_for_height(A->height) != A->bits) return CMRS_ERR_HEIGHT;
   if (A->strips != ceil_div(A->rows, A->height)) return CMRS_ERR_ARG;

@@ -282,6 +282,7 @@ extern "C" int cmrs_pad_workspace(const cmrs_matrix *A, int slots, size_t *bytes
 
 extern "C" int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_ptr_padded, int32_t *nnz_padded,
                                void *workspace, size_t workspace_bytes, void *stream) {
+  CMRS_TRACE();
   int rc = check_pad_input(A, slots);
   if (rc) return rc;
   if (!strip_ptr_padded || !nnz_padded) return CMRS_ERR_ARG;
@@ -316,6 +317,7 @@ extern "C" int cmrs_pad_layout(const cmrs_matrix *A, int slots, int32_t *strip_p
 
 extern "C" int cmrs_pad_fill(const cmrs_matrix *A, int slots, const int32_t *strip_ptr_padded, int32_t nnz_padded,
                              uint32_t *col_packed_out, void *val_out, void *stream, cmrs_matrix *out) {
+  CMRS_TRACE();
   int rc = check_pad_input(A, slots);
   if (rc) return rc;
   if (!out || nnz_padded < 0 || (nnz_padded & 31)) return CMRS_ERR_ARG;

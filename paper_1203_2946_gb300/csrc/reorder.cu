@@ -104,6 +104,7 @@ size_t perm_ws_bytes(int rows) { return 256 + align256((size_t)(rows > 0 ? rows 
 using namespace cmrs;
 
 extern "C" int cmrs_row_order(int rows, const int32_t *row_ptr, int window, int32_t *perm_out, void *stream) {
+  CMRS_TRACE();
   if (rows < 0 || window < 1 || window > kOrderMax) return CMRS_ERR_ARG;
   if (rows == 0) return CMRS_OK;
   if (!row_ptr || !perm_out) return CMRS_ERR_ARG;
@@ -126,6 +127,7 @@ extern "C" int cmrs_permute_csr_workspace(int rows, size_t *bytes) {
 extern "C" int cmrs_permute_csr(int rows, int nnz, const int32_t *row_ptr, const int32_t *col_ind, const void *val,
                                 int val_dtype, const int32_t *perm, int32_t *row_ptr_out, int32_t *col_ind_out,
                                 void *val_out, void *workspace, size_t workspace_bytes, void *stream) {
+  CMRS_TRACE();
   if (rows < 0 || nnz < 0) return CMRS_ERR_ARG;
   if (val && val_dtype != CMRS_F64 && val_dtype != CMRS_F32) return CMRS_ERR_ARG;
   if (!row_ptr || !row_ptr_out || (rows > 0 && !perm)) return CMRS_ERR_ARG;

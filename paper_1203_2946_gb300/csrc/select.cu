@@ -344,6 +344,7 @@ extern "C" int cmrs_features_workspace(int rows, size_t *bytes) {
 
 extern "C" int cmrs_features(int rows, int nnz, const int32_t *row_ptr, const int32_t *col_ind, double *feat,
                              void *workspace, size_t workspace_bytes, void *stream) {
+  CMRS_TRACE();
   if (rows < 1 || nnz < 0 || !row_ptr || !feat || (nnz > 0 && !col_ind)) return CMRS_ERR_ARG;
   if (!workspace || workspace_bytes < features_ws(rows) || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return CMRS_ERR_WORKSPACE;
@@ -368,6 +369,7 @@ extern "C" int64_t cmrs_mlp_param_count(int nin, int nh, int nout) {
 // acts layout: Z1[B][nh], H1[B][nh], Z2[B][nh], H2[B][nh], O[B][nout]
 extern "C" int cmrs_mlp_forward(int B, int nin, int nh, int nout, const float *X, const float *params, float *acts,
                                 void *stream) {
+  CMRS_TRACE();
   if (B < 1 || nin < 1 || nh < 1 || nout < 1 || !X || !params || !acts) return CMRS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   const float *W1 = params, *b1 = W1 + (size_t)nh * nin, *W2 = b1 + nh, *b2 = W2 + (size_t)nh * nh, *W3 = b2 + nh,
@@ -386,6 +388,7 @@ extern "C" int cmrs_mlp_forward(int B, int nin, int nh, int nout, const float *X
 extern "C" int cmrs_mlp_backward(int B, int nin, int nh, int nout, const float *X, const float *T,
                                  const float *params, const float *acts, float *grads, float *scratch, float *loss,
                                  void *stream) {
+  CMRS_TRACE();
   if (B < 1 || nin < 1 || nh < 1 || nout < 1 || !X || !T || !params || !acts || !grads || !scratch)
     return CMRS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
@@ -408,6 +411,7 @@ extern "C" int cmrs_mlp_backward(int B, int nin, int nh, int nout, const float *
 
 extern "C" int cmrs_mlp_adam(int n, float *params, const float *grads, float *m, float *v, int step, float lr,
                              float beta1, float beta2, float eps, void *stream) {
+  CMRS_TRACE();
   if (n < 1 || !params || !grads || !m || !v || step < 1) return CMRS_ERR_ARG;
   const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
   k_adam<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(n, params, grads, m, v, lr, beta1, beta2, eps, c1, c2);
@@ -451,6 +455,7 @@ __global__ void k_fill(float *p, long long n, float v) {
 extern "C" int cmrs_select_strip(int rows, int cols, int nnz, const int32_t *row_ptr, const int32_t *col_ind,
                                  const cmrs_selector *model, int *height_out, int *variant_out, int *slots_out,
                                  void *workspace, size_t workspace_bytes, void *stream) {
+  CMRS_TRACE();
   if (rows < 1 || cols < 1 || nnz < 0 || !row_ptr || !height_out || !variant_out || !slots_out) return CMRS_ERR_ARG;
   const int exhaustive = model == nullptr;
   const size_t need = select_ws(rows, cols, nnz, exhaustive);

@@ -258,6 +258,7 @@ struct cmrs_spmm_plan {
 };
 
 extern "C" int cmrs_spmm(const cmrs_matrix *A, int k, const float *X, float *Y, void *stream) {
+  CMRS_TRACE();
   int rc = check_item(A, k, X, Y);
   if (rc) return rc;
   if (A->rows == 0) return CMRS_OK;
@@ -316,6 +317,7 @@ extern "C" int cmrs_spmm_plan_workspace(int batch, const cmrs_matrix *const *A, 
 extern "C" int cmrs_spmm_plan_create(int batch, const cmrs_matrix *const *A, const int32_t *k, const float *const *X,
                                      float *const *Y, int work_target, int use_graph, void *workspace,
                                      size_t workspace_bytes, void *stream, cmrs_spmm_plan **out) {
+  CMRS_TRACE();
   if (!out) return CMRS_ERR_ARG;
   *out = nullptr;
   if (batch < 1 || !A || !k || !X || !Y || work_target < 1) return CMRS_ERR_ARG;
@@ -379,6 +381,7 @@ extern "C" int cmrs_spmm_plan_create(int batch, const cmrs_matrix *const *A, con
 }
 
 extern "C" int cmrs_spmm_batched(cmrs_spmm_plan *p, void *stream) {
+  CMRS_TRACE();
   if (!p) return CMRS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   if (p->exec) {
@@ -412,6 +415,7 @@ extern "C" int cmrs_spmm_plan_destroy(cmrs_spmm_plan *p) {
 extern "C" int cmrs_spmm_autotune(int batch, const cmrs_matrix *const *A, const int32_t *k, const float *const *X,
                                   float *const *Y, const int *candidates, int ncand, int reps, void *workspace,
                                   size_t workspace_bytes, void *stream, int *best_target, float *best_ms) {
+  CMRS_TRACE();
   if (!candidates || ncand < 1 || reps < 1 || !best_target) return CMRS_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   cudaEvent_t e0, e1;

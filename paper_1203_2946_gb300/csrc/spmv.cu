@@ -1399,16 +1399,19 @@ int spmv_impl(const cmrs_matrix *A, const void *x, void *y, const int32_t *row_m
 
 extern "C" int cmrs_spmv(const cmrs_matrix *A, const void *x, void *y, int variant, void *workspace,
                          size_t workspace_bytes, void *stream) {
+  CMRS_TRACE();
   return spmv_impl(A, x, y, nullptr, variant, workspace, workspace_bytes, stream);
 }
 
 extern "C" int cmrs_spmv_rows(const cmrs_matrix *A, const void *x, void *y, const int32_t *row_map, int variant,
                               void *workspace, size_t workspace_bytes, void *stream) {
+  CMRS_TRACE();
   if (!row_map && A && A->rows > 0) return CMRS_ERR_ARG;
   return spmv_impl(A, x, y, row_map, variant, workspace, workspace_bytes, stream);
 }
 
 extern "C" int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, void *stream) {
+  CMRS_TRACE();
   (void)A;
   (void)variant;
   if (!workspace) return CMRS_ERR_ARG;
@@ -1424,6 +1427,36 @@ extern "C" int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *wo
     CMRS_CUDA_TRY(cudaMemsetAsync(const_cast<void *>(workspace), 0, 4, st));
     return CMRS_ERR_ARG;
   }
+  return CMRS_OK;
+}
+
+// ============================================================== wait probe
+// One warp runs the bounded mbarrier wait of the staged kernels on a phase
+// that only an arrival of its own completes (no copy is issued, so none is in
+// flight when it leaves).  Without the arrival every lane gives up after
+// `tries` tries and the timeout bit is set as the SpMV kernels set it.
+namespace cmrs {
+namespace {
+__global__ void k_wait_probe(uint32_t tries, int arrive, uint32_t *status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive(&bar);
+  const bool ok = mbar_wait_bounded(&bar, 0, tries);
+  if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+}  // namespace
+}  // namespace cmrs
+
+extern "C" int cmrs_wait_probe(void *workspace, uint32_t tries, int arrive, void *stream) {
+  CMRS_TRACE();
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || tries < 1 || tries > 65536)
+    return CMRS_ERR_ARG;
+  k_wait_probe<<<1, 32, 0, as_stream(stream)>>>(tries, arrive != 0, static_cast<uint32_t *>(workspace));
+  CMRS_LAUNCH_CHECK();
   return CMRS_OK;
 }
 
@@ -1458,6 +1491,7 @@ int noalloc_scratch(void **out) {
 }  // namespace
 
 extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, void *stream) {
+  CMRS_TRACE();
   int rc = check_matrix(A);
   if (rc) return rc;
   if (A->flags & (CMRS_SORTED | CMRS_PADDED)) return CMRS_ERR_UNSUPPORTED;

@@ -258,6 +258,49 @@ def test_spmv_repeatable(b):
             b.cmrs_spmv_check(M, var)
 
 
+def test_wait_timeout_reported_and_context_usable(b):
+    """A bounded in-kernel mbarrier wait that nothing completes gives up, the
+    timeout bit reaches the host as CMRS_ERR_TIMEOUT once (the check clears
+    it), and the context still computes correct products afterwards.  Also
+    measures how long one failed try takes, hence how long the kernels'
+    2^18-try limit lets a wait last (about a second is the aim)."""
+    a, x = inputs.workload_laplacian_64()
+    M = convert(b, a, 4)
+    var = b.CMRS_VARIANT_MERGE
+    ws = M.spmv_workspace(var)
+    # the phase completed by the probe's own arrival: no timeout
+    b.cmrs_wait_probe(ws, 64, arrive=True)
+    b.cmrs_spmv_check(M, var)
+    # left open: the wait gives up after `tries` tries; the probe grows
+    # `tries` only while the time per try keeps a probe under ~0.2 s
+    per_try, tries = None, 16
+    while True:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.cmrs_wait_probe(ws, tries, arrive=False)
+        e1.record()
+        torch.cuda.synchronize()
+        per_try = e0.elapsed_time(e1) * 1e-3 / tries
+        with pytest.raises(b.CmrsError) as ei:
+            b.cmrs_spmv_check(M, var)
+        assert ei.value.code == 8  # CMRS_ERR_TIMEOUT
+        b.cmrs_spmv_check(M, var)  # cleared by the first check
+        if tries >= 65536 or per_try * tries * 16 > 0.2:
+            break
+        tries *= 16
+    limit_s = per_try * (1 << 18)
+    print("\nbounded wait: %d tries in %.3f ms, %.3f us per try; the kernels' 2^18 tries: %.2f s"
+          % (tries, per_try * tries * 1e3, per_try * 1e6, limit_s))
+    assert 0.01 < limit_s < 10
+    # the context is intact: the product still matches the oracle
+    for v in VARIANTS:
+        check_spmv(b, M, a, x, v, 0)
+    with pytest.raises(b.CmrsError):
+        b.cmrs_wait_probe(ws, 0, arrive=False)
+    with pytest.raises(b.CmrsError):
+        b.cmrs_wait_probe(ws, 65537, arrive=False)
+
+
 def test_laplacian_64_config(b):
     """5-point Laplacian 64x64, FP64, h = 4: conversion + SpMV against the oracle."""
     a, x = inputs.workload_laplacian_64()
