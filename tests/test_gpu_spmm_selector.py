@@ -85,6 +85,69 @@ def test_spmm_batched(b, use_graph, target):
     plan.close()
 
 
+def _batched_member(spec):
+    """One matrix of the 256-matrix banded batch, and the oracle's FP64 values
+    (with |A||x|) of a sample of its rows for every column of its X: the first
+    and last rows, rows on both sides of a strip edge, and random rows.  Runs
+    in a spawned worker."""
+    a, X = inputs.batched_banded(spec)
+    n = a.rows
+    rng = np.random.default_rng(spec["seed"] + 2)
+    rows = np.unique(np.concatenate([[0, 1, 3, 4, n - 2, n - 1], rng.integers(0, n, 58)]))
+    lens = np.diff(a.row_ptr)[rows]
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    idx = np.concatenate([np.arange(a.row_ptr[r], a.row_ptr[r + 1]) for r in rows])
+    ci, v = a.col_ind[idx], a.val[idx].astype(np.float32).astype(np.float64)
+    ref = np.empty((rows.size, X.shape[1]))
+    scale = np.empty_like(ref)
+    for c in range(X.shape[1]):
+        ref[:, c], scale[:, c] = orc.csr_spmv(rp, ci, v, X[:, c].astype(np.float64))
+    return a.row_ptr, a.col_ind, a.val, X, rows, ref, scale, lens
+
+
+def test_spmm_batched_full_size(b):
+    """The batched workload at full size: 256 banded-random matrices (n
+    1,000..200,000, bandwidth 64..2,048, 10..60 entries per row, k in
+    {1, 4, 8, 32}), in the configuration the benchmark times: height 4,
+    autotuned work target, one graph-captured persistent launch.  Sampled rows
+    of every matrix, every right-hand side, against the FP64 oracle; every
+    row written; a second replay bit-identical."""
+    import multiprocessing as mp
+    import os
+    orc.lib()  # built before the workers load it
+    specs = inputs.batched_banded_specs()
+    assert len(specs) == 256
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        parts = pool.map(_batched_member, specs, chunksize=4)
+    mats, Xs, Ys = [], [], []
+    for rp, ci, val, X, *_ in parts:
+        n = rp.size - 1
+        mats.append(b.cmrs_from_csr(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(),
+                                    torch.from_numpy(val).cuda(), n, 4, dtype=b.CMRS_F32))
+        Xs.append(torch.from_numpy(X).cuda())
+        Ys.append(torch.empty((n, X.shape[1]), dtype=torch.float32, device="cuda"))
+    assert sum(M.nnz for M in mats) > 500_000_000
+    best, _ = b.cmrs_spmm_autotune(mats, Xs, Ys, candidates=(2048, 8192, 32768, 131072), reps=3)
+    plan = b.SpmmPlan(mats, Xs, Ys, work_target=best, use_graph=True)
+    for Y in Ys:
+        Y.fill_(float("nan"))
+    b.cmrs_spmm_batched(plan)
+    got = []
+    for Y, p in zip(Ys, parts):
+        assert not torch.isnan(Y).any()
+        got.append(Y[torch.from_numpy(p[4]).cuda()].cpu().numpy())
+    for Y in Ys:
+        Y.fill_(float("nan"))
+    b.cmrs_spmm_batched(plan)
+    for i, (Y, p, g) in enumerate(zip(Ys, parts, got)):
+        rows, ref, scale, lens = p[4], p[5], p[6], p[7]
+        assert np.array_equal(Y[torch.from_numpy(rows).cuda()].cpu().numpy(), g)
+        tol = (lens[:, None] + 2) * 2.0**-24 * scale
+        err = np.abs(g.astype(np.float64) - ref)
+        assert (err <= tol).all(), (i, np.argwhere(err > tol)[:5])
+    plan.close()
+
+
 def test_spmm_autotune(b):
     mats, Xs, Ys, host = small_batch(b, 12, seed=5)
     best, ms = b.cmrs_spmm_autotune(mats, Xs, Ys, candidates=(1024, 16384), reps=3)
