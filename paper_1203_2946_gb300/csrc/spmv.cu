@@ -685,13 +685,22 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
           xv[j] = ld_x(x + (c[j] >> bits));
         }
       }
-      // row of every entry: integer work only (the strip walk may diverge)
+      // row of every entry: integer work only.  When all of the thread's
+      // entries lie in the strip holding k0 (the usual case) no StripPtr walk
+      // is needed; otherwise the walk may diverge.
       uint32_t rw[kMergeE];
+      if (k1 <= next) {
+        const uint32_t r0 = (uint32_t)cur * (uint32_t)height;
 #pragma unroll
-      for (int j = 0; j < kMergeE; ++j) {
-        if (j < n) {
-          while (k0 + j >= next) next = sp[++cur + 1];
-          rw[j] = (uint32_t)cur * (uint32_t)height + (c[j] & mask);
+        for (int j = 0; j < kMergeE; ++j)
+          if (j < n) rw[j] = r0 + (c[j] & mask);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kMergeE; ++j) {
+          if (j < n) {
+            while (k0 + j >= next) next = sp[++cur + 1];
+            rw[j] = (uint32_t)cur * (uint32_t)height + (c[j] & mask);
+          }
         }
       }
       // rows before the first entry of the matrix are empty
@@ -719,11 +728,18 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
           run_row = rw[j];
         }
       }
-      // rows with no entries between two runs of this thread
+      // rows with no entries between two runs of this thread (rows are
+      // non-decreasing along the entries; one test finds whether any is skipped)
+      bool gap = false;
 #pragma unroll
       for (int j = 1; j < kMergeE; ++j)
-        if (j < n)
-          for (uint32_t g = rw[j - 1] + 1; g < rw[j] && g < (uint32_t)rows; ++g) y[g] = A(0);
+        if (j < n) gap = gap || rw[j] > rw[j - 1] + 1;
+      if (gap) {
+#pragma unroll
+        for (int j = 1; j < kMergeE; ++j)
+          if (j < n)
+            for (uint32_t g = rw[j - 1] + 1; g < rw[j] && g < (uint32_t)rows; ++g) y[g] = A(0);
+      }
       // the entry after this thread's last one: same row?
       long long next_row = rows;
       if (k1 < nnz) {
