@@ -673,36 +673,42 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
         cont_in = (cprev & mask) == (cp[k0 - base] & mask);
       }
       const int n = (int)(k1 - k0);  // 1 .. kMergeE
-      // operands first, so that the x loads of the run are in flight together
-      uint32_t c[kMergeE];
+      // The walk over the thread's entries is compiled twice: for a thread
+      // holding all kMergeE entries (every thread but the matrix's last one
+      // with entries) the per-entry guards j < n vanish.
+      uint32_t c[kMergeE], rw[kMergeE];
       A xv[kMergeE], v[kMergeE];
-#pragma unroll
-      for (int j = 0; j < kMergeE; ++j) {
-        if (j < n) {
-          const long long i = k0 + j - base;
-          c[j] = cp[i];
-          v[j] = Form<DT>::value(vh, vl, i);
-          xv[j] = ld_x(x + (c[j] >> bits));
-        }
-      }
-      // row of every entry: integer work only.  When all of the thread's
-      // entries lie in the strip holding k0 (the usual case) no StripPtr walk
-      // is needed; otherwise the walk may diverge.
-      uint32_t rw[kMergeE];
-      if (k1 <= next) {
-        const uint32_t r0 = (uint32_t)cur * (uint32_t)height;
-#pragma unroll
-        for (int j = 0; j < kMergeE; ++j)
-          if (j < n) rw[j] = r0 + (c[j] & mask);
-      } else {
+      // operands first, so that the x loads of the run are in flight together;
+      // then the row of every entry: integer work only.  When all of the
+      // thread's entries lie in the strip holding k0 (the usual case) no
+      // StripPtr walk is needed; otherwise the walk may diverge.
+      auto operands_and_rows = [&](auto full) {
 #pragma unroll
         for (int j = 0; j < kMergeE; ++j) {
-          if (j < n) {
-            while (k0 + j >= next) next = sp[++cur + 1];
-            rw[j] = (uint32_t)cur * (uint32_t)height + (c[j] & mask);
+          if (decltype(full)::value || j < n) {
+            const long long i = k0 + j - base;
+            c[j] = cp[i];
+            v[j] = Form<DT>::value(vh, vl, i);
+            xv[j] = ld_x(x + (c[j] >> bits));
           }
         }
-      }
+        if (k1 <= next) {
+          const uint32_t r0 = (uint32_t)cur * (uint32_t)height;
+#pragma unroll
+          for (int j = 0; j < kMergeE; ++j)
+            if (decltype(full)::value || j < n) rw[j] = r0 + (c[j] & mask);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kMergeE; ++j) {
+            if (decltype(full)::value || j < n) {
+              while (k0 + j >= next) next = sp[++cur + 1];
+              rw[j] = (uint32_t)cur * (uint32_t)height + (c[j] & mask);
+            }
+          }
+        }
+      };
+      if (n == kMergeE) operands_and_rows(std::true_type{});
+      else operands_and_rows(std::false_type{});
       // rows before the first entry of the matrix are empty
       if (k0 == 0)
         for (uint32_t g = 0; g < rw[0] && g < (uint32_t)rows; ++g) y[g] = A(0);
@@ -715,31 +721,35 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
       A head_sum = A(0);
       bool first = true;  // the current run is this thread's first
       uint32_t run_row = rw[0];
+      auto sums_and_gaps = [&](auto full) {
 #pragma unroll
-      for (int j = 1; j < kMergeE; ++j) {
-        if (j < n) {
-          const bool nw = rw[j] != rw[j - 1];
-          const bool to_head = nw && first && cont_in;  // first run continues a row from before k0
-          head_sum = to_head ? acc : head_sum;
-          if (nw && !to_head && rw[j - 1] < (uint32_t)rows) y[rw[j - 1]] = acc;
-          first = first && !nw;
-          acc = nw ? A(0) : acc;
-          acc = fma_acc(v[j], xv[j], acc);
-          run_row = rw[j];
+        for (int j = 1; j < kMergeE; ++j) {
+          if (decltype(full)::value || j < n) {
+            const bool nw = rw[j] != rw[j - 1];
+            const bool to_head = nw && first && cont_in;  // first run continues a row from before k0
+            head_sum = to_head ? acc : head_sum;
+            if (nw && !to_head && rw[j - 1] < (uint32_t)rows) y[rw[j - 1]] = acc;
+            first = first && !nw;
+            acc = nw ? A(0) : acc;
+            acc = fma_acc(v[j], xv[j], acc);
+            run_row = rw[j];
+          }
         }
-      }
-      // rows with no entries between two runs of this thread (rows are
-      // non-decreasing along the entries; one test finds whether any is skipped)
-      bool gap = false;
-#pragma unroll
-      for (int j = 1; j < kMergeE; ++j)
-        if (j < n) gap = gap || rw[j] > rw[j - 1] + 1;
-      if (gap) {
+        // rows with no entries between two runs of this thread (rows are
+        // non-decreasing along the entries; one test finds whether any is skipped)
+        bool gap = false;
 #pragma unroll
         for (int j = 1; j < kMergeE; ++j)
-          if (j < n)
-            for (uint32_t g = rw[j - 1] + 1; g < rw[j] && g < (uint32_t)rows; ++g) y[g] = A(0);
-      }
+          if (decltype(full)::value || j < n) gap = gap || rw[j] > rw[j - 1] + 1;
+        if (gap) {
+#pragma unroll
+          for (int j = 1; j < kMergeE; ++j)
+            if (decltype(full)::value || j < n)
+              for (uint32_t g = rw[j - 1] + 1; g < rw[j] && g < (uint32_t)rows; ++g) y[g] = A(0);
+        }
+      };
+      if (n == kMergeE) sums_and_gaps(std::true_type{});
+      else sums_and_gaps(std::false_type{});
       // the entry after this thread's last one: same row?
       long long next_row = rows;
       if (k1 < nnz) {
