@@ -78,6 +78,66 @@ def test_host_validation_paths(L):
     assert L.cmrs_wait_probe(ctypes.c_void_p(4096), 65537, 0, None) == 1
 
 
+def test_argument_checks_before_device_work(L):
+    """Conversion, SpMM, feature, network and selector entry points: bad
+    arguments are rejected, and the size queries answer, on the host alone
+    (no device pointer is dereferenced on these paths)."""
+    from paper_1203_2946_gb300 import binding as b
+    n = ctypes.c_size_t()
+    # CRS -> CMRS size query: (rows, nnz, height, flags, dtype, bytes)
+    assert L.cmrs_from_csr_workspace(10, 5, 4, 0, 0, None) == 1
+    assert L.cmrs_from_csr_workspace(-1, 5, 4, 0, 0, ctypes.byref(n)) == 1
+    assert L.cmrs_from_csr_workspace(10, 5, 4, 0, 9, ctypes.byref(n)) == 1
+    assert L.cmrs_from_csr_workspace(10, 5, 0, 0, 0, ctypes.byref(n)) == 2
+    assert L.cmrs_from_csr_workspace(10, 5, 33, 0, 0, ctypes.byref(n)) == 2
+    assert L.cmrs_from_csr_workspace(10, 5, 4, 0, 0, ctypes.byref(n)) == 0 and n.value > 0
+    assert L.cmrs_to_csr_workspace(None, ctypes.byref(n)) == 1
+    # SpMM: FP32 unsorted, unpadded strips only
+    m = b.cmrs_matrix()
+    m.rows, m.cols, m.nnz, m.height, m.strips, m.bits, m.dtype, m.flags = 10, 10, 5, 4, 3, 4, 1, 0
+    m.strip_ptr = m.col_packed = m.val = 256  # never dereferenced on these paths
+    p = ctypes.c_void_p(256)
+    assert L.cmrs_spmm(None, 4, p, p, None) == 1
+    assert L.cmrs_spmm(ctypes.byref(m), 0, p, p, None) == 1
+    m.dtype = 0
+    assert L.cmrs_spmm(ctypes.byref(m), 4, p, p, None) == 6  # FP64
+    m.dtype, m.flags = 1, 1
+    assert L.cmrs_spmm(ctypes.byref(m), 4, p, p, None) == 6  # sorted strips
+    m.flags, m.bits = 0, 5
+    assert L.cmrs_spmm(ctypes.byref(m), 4, p, p, None) == 2  # bits do not match the height
+    m.bits, m.strips = 4, 2
+    assert L.cmrs_spmm(ctypes.byref(m), 4, p, p, None) == 1  # strips != ceil(rows / height)
+    m.strips = 3
+    assert L.cmrs_spmm(ctypes.byref(m), 4, None, p, None) == 1  # X missing
+    z = b.cmrs_matrix()
+    z.rows, z.cols, z.nnz, z.height, z.strips, z.bits, z.dtype = 0, 10, 0, 4, 0, 4, 1
+    assert L.cmrs_spmm(ctypes.byref(z), 4, None, None, None) == 0  # no rows: nothing to do
+    # batched plan size query
+    A = (ctypes.c_void_p * 1)(ctypes.addressof(m))
+    k = (ctypes.c_int32 * 1)(4)
+    assert L.cmrs_spmm_plan_workspace(-1, A, k, 1024, ctypes.byref(n)) == 1
+    assert L.cmrs_spmm_plan_workspace(1, A, k, 0, ctypes.byref(n)) == 1
+    assert L.cmrs_spmm_plan_workspace(1, None, k, 1024, ctypes.byref(n)) == 1
+    k0 = (ctypes.c_int32 * 1)(0)
+    assert L.cmrs_spmm_plan_workspace(1, A, k0, 1024, ctypes.byref(n)) == 1
+    assert L.cmrs_spmm_plan_workspace(1, A, k, 1024, ctypes.byref(n)) == 0 and n.value > 0 and n.value % 256 == 0
+    # features, network, selector
+    assert L.cmrs_features_workspace(-1, ctypes.byref(n)) == 1
+    assert L.cmrs_features_workspace(10, None) == 1
+    assert L.cmrs_features_workspace(10, ctypes.byref(n)) == 0 and n.value > 0
+    assert L.cmrs_features(0, 5, p, p, p, p, 1 << 20, None) == 1
+    assert L.cmrs_features(10, 5, p, p, p, None, 1 << 20, None) == 7  # no workspace
+    assert L.cmrs_features(10, 5, p, p, p, ctypes.c_void_p(256 + 16), 1 << 20, None) == 7  # misaligned
+    assert L.cmrs_mlp_param_count(0, 64, 21) == -1
+    # two hidden layers: nin*nh + nh, nh*nh + nh, nh*nout + nout
+    assert L.cmrs_mlp_param_count(24, 64, 21) == 24 * 64 + 64 + 64 * 64 + 64 + 64 * 21 + 21
+    assert L.cmrs_mlp_forward(0, 24, 64, 21, p, p, p, None) == 1
+    assert L.cmrs_mlp_forward(4, 24, 64, 21, None, p, p, None) == 1
+    assert L.cmrs_select_strip_workspace(0, 10, 5, 0, ctypes.byref(n)) == 1
+    assert L.cmrs_select_strip_workspace(10, 10, 5, 0, None) == 1
+    assert L.cmrs_select_strip_workspace(10, 10, 5, 0, ctypes.byref(n)) == 0 and n.value > 0
+
+
 def test_auto_variant_rule(L):
     """CMRS_VARIANT_AUTO: STRIP on sorted strips; otherwise MERGE for mean row
     length < 2 or > 32 or a strip above 8 x height x mean (or unknown), ROW
