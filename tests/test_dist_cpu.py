@@ -65,3 +65,25 @@ def test_beta_minus_and_eta_match_eq_6_1():
         assert abs(e["eta_plus"] - bp / 1e-4 / 1e9 / 1000.0) < 1e-12
         assert abs(e["eta_minus"] - bm / 1e-4 / 1e9 / 1000.0) < 1e-12
         assert abs(e["beta_minus_gbs"] - bm / 1e-4 / 1e9) < 1e-9
+
+
+def test_reference_arm_line_contract():
+    """bench.py --impl reference: one JSON line timing the oracle on the host
+    cores, with the keys of the benchmark line, its own cpu_baseline and an
+    e2e block with no host-device copies (the 64x64 Laplacian: whole-matrix
+    steps of microseconds)."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "laplacian", "--height", "4", "--steps", "3", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["steps"] == 3 and line["warmup"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["vs_baseline"] is None
+    cb, e2e = line["cpu_baseline"], line["e2e"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
