@@ -298,8 +298,16 @@ int cmrs_spmv_rows(const cmrs_matrix *A, const void *x, void *y, const int32_t *
  * that device current), so make that first call before any stream capture.
  * Every call shares the one array, which keeps the last call's contents:
  * calls that may overlap on the GPU (two streams, two host threads) race and
- * their results are undefined.  Asynchronous on `stream`. */
+ * their results are undefined.  The cached address belongs to the device's
+ * current context: do not use this entry point after cudaDeviceReset in the
+ * same process.  Asynchronous on `stream`.
+ * The MERGE kernel's bounded waits record a give-up in a status word inside
+ * the array; the word is not cleared by the calls, so it holds every give-up
+ * since it was last read.  cmrs_spmv_noalloc_check reads and clears it for
+ * the current device (synchronising `stream`): CMRS_ERR_TIMEOUT means that
+ * some call since the last check left its y invalid. */
 int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, void *stream);
+int cmrs_spmv_noalloc_check(void *stream);
 
 /* Error status the SpMV kernels left in the status word inside `workspace`,
  * then cleared: CMRS_ERR_TIMEOUT if a bounded in-kernel wait gave up,
@@ -316,8 +324,11 @@ int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, vo
  * the kernel sets the timeout bit of the status word at the start of
  * `workspace` (device, caller-owned, >= 256 bytes, 256-byte aligned) and
  * returns.  cmrs_spmv_check on that workspace then reports CMRS_ERR_TIMEOUT
- * and clears the bit.  No copy is issued, so none is left in flight.
- * CMRS_ERR_ARG for a bad workspace or `tries`.  Asynchronous on `stream`. */
+ * and clears the bit.  workspace == NULL names the status word of the fixed
+ * array of cmrs_spmv_noalloc on the current device, which
+ * cmrs_spmv_noalloc_check then reports.  No copy is issued, so none is left
+ * in flight.  CMRS_ERR_ARG for a misaligned workspace or a bad `tries`.
+ * Asynchronous on `stream`. */
 int cmrs_wait_probe(void *workspace, uint32_t tries, int arrive, void *stream);
 
 /* ---- multi right-hand-side SpMM, single and batched ----------------------

@@ -89,6 +89,7 @@ def lib():
             "cmrs_spmv_check": ([M, i, vp, vp], i),
             "cmrs_wait_probe": ([vp, u, i, vp], i),
             "cmrs_spmv_noalloc": ([M, vp, vp, vp], i),
+            "cmrs_spmv_noalloc_check": ([vp], i),
             "cmrs_spmm": ([M, i, vp, vp, vp], i),
             "cmrs_spmm_plan_workspace": ([i, vp, vp, i, ctypes.POINTER(sz)], i),
             "cmrs_spmm_plan_create": ([i, vp, vp, vp, vp, i, i, vp, sz, vp, ctypes.POINTER(vp)], i),
@@ -301,6 +302,13 @@ def cmrs_spmv_noalloc(A: Matrix, x, y=None, stream=None):
         y = torch.empty(A.rows, dtype=A.x_dtype, device=x.device)
     _check(lib().cmrs_spmv_noalloc(A.ref(), _ptr(x), _ptr(y), _stream(stream)), "cmrs_spmv_noalloc")
     return y
+
+
+def cmrs_spmv_noalloc_check(stream=None):
+    """Reads and clears the status word of cmrs_spmv_noalloc's fixed array on
+    the current device; raises CmrsError(CMRS_ERR_TIMEOUT) if a call since the
+    last check gave up a bounded wait."""
+    _check(lib().cmrs_spmv_noalloc_check(_stream(stream)), "cmrs_spmv_noalloc_check")
 
 
 def cmrs_spmv_check(A: Matrix, variant=CMRS_VARIANT_AUTO, stream=None):

@@ -1477,10 +1477,18 @@ __global__ void k_wait_probe(uint32_t tries, int arrive, uint32_t *status) {
 }  // namespace
 }  // namespace cmrs
 
+namespace {
+int noalloc_scratch(void **out);
+}
+
 extern "C" int cmrs_wait_probe(void *workspace, uint32_t tries, int arrive, void *stream) {
   CMRS_TRACE();
-  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || tries < 1 || tries > 65536)
-    return CMRS_ERR_ARG;
+  if (tries < 1 || tries > 65536) return CMRS_ERR_ARG;
+  if (!workspace) {  // the status word of the fixed array of cmrs_spmv_noalloc
+    const int rc = noalloc_scratch(&workspace);
+    if (rc) return rc;
+  }
+  if (reinterpret_cast<uintptr_t>(workspace) & 255) return CMRS_ERR_ARG;
   k_wait_probe<<<1, 32, 0, as_stream(stream)>>>(tries, arrive != 0, static_cast<uint32_t *>(workspace));
   CMRS_LAUNCH_CHECK();
   return CMRS_OK;
@@ -1534,8 +1542,9 @@ extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, v
     CMRS_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)A->rows * (A->dtype == CMRS_F64 ? 8 : 4), st));
     return CMRS_OK;
   }
-  // the status word must start at zero; everything else is rewritten per call
-  CMRS_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256, st));
+  // The status word (zero at load) is not cleared here: a wait that gave up
+  // stays recorded until cmrs_spmv_noalloc_check reads it.  Everything else
+  // in the array is rewritten by every call.
   char *ws = reinterpret_cast<char *>(scratch);
   switch (A->dtype) {
     case CMRS_F64: return launch<CMRS_F64>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, sizeof(cmrs_noalloc_scratch), st);
@@ -1544,4 +1553,17 @@ extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, v
     case CMRS_BF16X2: return launch<CMRS_BF16X2>(A, x, y, nullptr, CMRS_VARIANT_MERGE, ws, sizeof(cmrs_noalloc_scratch), st);
   }
   return CMRS_ERR_ARG;
+}
+
+extern "C" int cmrs_spmv_noalloc_check(void *stream) {
+  CMRS_TRACE();
+  void *scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  uint32_t s = 0;
+  cudaStream_t st = as_stream(stream);
+  CMRS_CUDA_TRY(cudaMemcpyAsync(&s, scratch, 4, cudaMemcpyDeviceToHost, st));
+  CMRS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (s) CMRS_CUDA_TRY(cudaMemsetAsync(scratch, 0, 4, st));
+  return (s & ST_TIMEOUT) ? CMRS_ERR_TIMEOUT : CMRS_OK;
 }

@@ -249,6 +249,27 @@ def from_lengths(lengths, cols: int, seed: int = 0, dtype=np.float64) -> CSR:
     return _finish(rows, cols, lengths, col, val, "lengths_%d" % rows)
 
 
+def random_lengths_exact_nnz(nnz: int, max_len: int, cols: int, seed: int = 0) -> CSR:
+    """Rows of U{1..max_len} entries, as many as it takes to hold exactly
+    `nnz` entries (the last row shortened to fit); row i's j-th of L columns
+    is drawn uniformly from the stratum [j cols / L, (j + 1) cols / L), so the
+    columns are distinct and increasing.  Values U[-1, 1] FP32."""
+    r_len, r_col, r_val = _streams(seed, 3)
+    lengths = r_len.integers(1, max_len + 1, size=4 * nnz // (max_len + 1) + 64)
+    cum = np.cumsum(lengths)
+    rows = int(np.searchsorted(cum, nnz)) + 1
+    lengths = lengths[:rows].astype(np.int64)
+    lengths[-1] -= int(cum[rows - 1]) - nnz
+    L = np.repeat(lengths, lengths)
+    start = np.repeat(np.cumsum(lengths) - lengths, lengths)
+    j = np.arange(nnz, dtype=np.int64) - start
+    lo = j * cols // L
+    hi = (j + 1) * cols // L
+    col = lo + (r_col.random(nnz) * (hi - lo)).astype(np.int64)
+    val = r_val.uniform(-1.0, 1.0, nnz).astype(np.float32)
+    return _finish(rows, cols, lengths, col, val, "lengths_exact_%d" % nnz)
+
+
 # --------------------------------------------------------------------------- named workloads
 def workload_laplacian_64():
     """5-point Laplacian 64x64 (n=4,096, nnz=20,224), FP64, x U[-1,1] seed 0."""

@@ -72,7 +72,7 @@ def test_host_validation_paths(L):
     m.strips, m.bits = 3, 5
     assert L.cmrs_spmv_workspace(ctypes.byref(m), 0, ctypes.byref(n)) == 1
     # the wait probe checks its workspace and try count before any launch
-    assert L.cmrs_wait_probe(None, 16, 0, None) == 1
+    assert L.cmrs_wait_probe(None, 0, 0, None) == 1  # tries checked before the fixed array is looked up
     assert L.cmrs_wait_probe(ctypes.c_void_p(4096 + 16), 16, 0, None) == 1
     assert L.cmrs_wait_probe(ctypes.c_void_p(4096), 0, 0, None) == 1
     assert L.cmrs_wait_probe(ctypes.c_void_p(4096), 65537, 0, None) == 1
