@@ -331,6 +331,34 @@ int cmrs_spmv_check(const cmrs_matrix *A, int variant, const void *workspace, vo
  * Asynchronous on `stream`. */
 int cmrs_wait_probe(void *workspace, uint32_t tries, int arrive, void *stream);
 
+/* Diagnostic, not in the paper: the floor of a product whose x reads are
+ * gathers (Section 6.3 reads a low eta_+ as x fetched many times over).
+ * Streams col[nnz] (device int32, a CRS column array) and val[nnz] (device
+ * float, or NULL for ones) once, in order, gathers x[col[k]] (device float
+ * [cols]) and adds val[k] * x[col[k]] into *out (device float, overwritten;
+ * the summation order is not fixed).  No row structure: the time of a call on
+ * a matrix's own columns is what any SpMV kernel pays for that matrix's
+ * gathers and streams alone.  A column outside [0, cols) reads x[cols - 1].
+ * CMRS_ERR_ARG for negative sizes or missing pointers.  Asynchronous. */
+int cmrs_gather_probe(int nnz, int cols, const int32_t *col, const float *val, const float *x, float *out,
+                      void *stream);
+
+/* ---- strip sharding over several GPUs --------------------------------------
+ * Strips are independent (Section 4: a strip's warp reads only its own
+ * entries and writes only its own rows of y), so a product can be split into
+ * contiguous ranges of whole strips, one per device; every device multiplies
+ * its range once it holds all of x, and y needs no reduction.
+ * cmrs_shard_rows: bounds[p] .. bounds[p+1] are the rows of part p, for
+ * p < parts (bounds: host int32 [parts + 1], bounds[0] = 0, bounds[parts] =
+ * rows).  Each inner bound is a strip start (a multiple of height, or rows),
+ * chosen as the first strip start at which the weight before it -- entries
+ * plus rows -- reaches ceil(p * total / parts); parts may be empty when
+ * there are fewer strips than parts.  row_ptr: host int32 [rows + 1], a CRS
+ * row pointer (RowPtr[0] = 0, non-decreasing; only RowPtr[0] is checked).
+ * Host only, pure.  CMRS_ERR_ARG for bad sizes or pointers, CMRS_ERR_HEIGHT
+ * for a height outside 1..32, CMRS_ERR_CSR_INVALID if RowPtr[0] != 0. */
+int cmrs_shard_rows(int rows, const int32_t *row_ptr, int height, int parts, int32_t *bounds);
+
 /* ---- multi right-hand-side SpMM, single and batched ----------------------
  * Y = A X for CMRS_F32 matrices with unsorted strips; X device [cols][k] and
  * Y device [rows][k], row-major FP32, FP32 accumulation.  Not in the paper:
@@ -376,14 +404,21 @@ int cmrs_spmm_autotune(int batch, const cmrs_matrix *const *A, const int32_t *k,
  * and 20 mean the modified CMRS of Section 6.6 (variant CMRS_VARIANT_PADDED)
  * at (height, slots) = (32, 1), (32, 2) and (16, 8).  The network outputs a
  * predicted cost per choice and the smallest wins. */
-#define CMRS_NFEAT 24
+#define CMRS_NFEAT 32
 #define CMRS_SEL_CHOICES 21
 
 /* Features (device double[CMRS_NFEAT]) of a CRS matrix (device row_ptr,
  * col_ind), from exact integer sums: log2 rows, log2 nnz, log2(1+mu), row
  * length CV, log2(1+max row), empty-row fraction, 8 row-length bins,
  * |col-row| statistics, equal-length neighbour fraction, per-strip column
- * spread for h = 1..32.  Asynchronous. */
+ * spread for h = 1..32 (features 0..23); log2(items / nnz) of the modified
+ * CMRS of Section 6.6 at (height, slots) = (32, 1), (32, 2), (16, 8), a strip
+ * of n_s entries with longest row m_s taking max(ceil(n_s/32),
+ * ceil(m_s/slots)) passes of 32 items (24..26); the fraction of entries in
+ * rows of at least 32, 512 and 8192 entries (27..29); the spread (std / mean)
+ * and log2(1 + max / mean) of the entry counts of 32-row strips (30, 31).
+ * All but the first three describe the matrix's shape, not its size.
+ * Asynchronous. */
 int cmrs_features_workspace(int rows, size_t *bytes);
 int cmrs_features(int rows, int nnz, const int32_t *row_ptr, const int32_t *col_ind, double *feat,
                   void *workspace, size_t workspace_bytes, void *stream);

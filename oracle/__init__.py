@@ -15,7 +15,7 @@ _lib = None
 
 ORC_OK, ORC_BAD_HEIGHT, ORC_BAD_CSR, ORC_COL_OVERFLOW, ORC_BAD_ARG = 0, 1, 2, 3, 4
 F64, F32, BF16, BF16X2 = 0, 1, 2, 3
-NFEAT = 24
+NFEAT = 32
 
 
 def lib():

@@ -358,7 +358,7 @@ void orc_beta(double nnz, double rows, double strips, double s_v, double s_i,
 /* ------------------------------------------------------------------------ */
 /* Strip selector (not in the paper; Section 6.2 tunes height by brute force
  * and Section 6.7 measures what per-matrix tuning gains).  The selector reads
- * 24 features of a CRS matrix, computed here with plain loops and exact
+ * 32 features of a CRS matrix, computed here with plain loops and exact
  * integer sums:
  *   f0  log2(rows)                 f1  log2(max(nnz, 1))
  *   f2  log2(1 + mu), mu = nnz/rows
@@ -371,8 +371,17 @@ void orc_beta(double nnz, double rows, double strips, double s_v, double s_i,
  *   f16 fraction of entries with |col - row| <= 64
  *   f17 fraction of rows i >= 1 with the same length as row i-1
  *   f18..f23 for h = 1, 2, 4, 8, 16, 32: log2(1 + mean over non-empty strips
- *           of (max col - min col) within the strip) */
-#define ORC_NFEAT 24
+ *           of (max col - min col) within the strip)
+ *   f24..f26 log2(items / nnz) of the modified CMRS (Section 6.6) at
+ *           (height, M) = (32, 1), (32, 2), (16, 8): a strip of n_s entries
+ *           whose longest row has m_s becomes max(ceil(n_s/32), ceil(m_s/M))
+ *           passes of 32 items (the fewest possible); 0 when nnz = 0
+ *   f27..f29 fraction of the entries that lie in rows of at least 32, 512
+ *           and 8192 entries
+ *   f30 sigma(n_32) / max(mean n_32, 1), n_32 the entries of a strip of 32
+ *       rows, over the ceil(rows/32) strips (population std)
+ *   f31 log2(1 + max n_32 / max(mean n_32, 1)) */
+#define ORC_NFEAT 32
 void orc_features(int rows, int nnz, const int32_t *row_ptr,
                   const int32_t *col_ind, double *f) {
   uint64_t sum_l2 = 0, max_l = 0, empty = 0, same = 0, near = 0;
@@ -430,6 +439,47 @@ void orc_features(int rows, int nnz, const int32_t *row_ptr,
     }
     f[18 + e] = log2(1.0 + (nonempty > 0 ? (double)spread / (double)nonempty : 0.0));
   }
+  /* the modified CMRS item counts (f24..f26) and the 32-row strip sizes */
+  static const int pad_h[3] = {32, 32, 16}, pad_m[3] = {1, 2, 8};
+  for (int q = 0; q < 3; ++q) {
+    uint64_t items = 0;
+    for (int s = 0; s * pad_h[q] < rows; ++s) {
+      int r1 = (s + 1) * pad_h[q] < rows ? (s + 1) * pad_h[q] : rows;
+      uint64_t ns = 0, ms = 0;
+      for (int i = s * pad_h[q]; i < r1; ++i) {
+        uint64_t l = (uint64_t)(row_ptr[i + 1] - row_ptr[i]);
+        ns += l;
+        if (l > ms) ms = l;
+      }
+      uint64_t by_items = (ns + 31) / 32, by_row = (ms + (uint64_t)pad_m[q] - 1) / (uint64_t)pad_m[q];
+      items += 32 * (by_items > by_row ? by_items : by_row);
+    }
+    f[24 + q] = nnz > 0 ? log2((double)items / z) : 0.0;
+  }
+  uint64_t e32 = 0, e512 = 0, e8192 = 0;
+  for (int i = 0; i < rows; ++i) {
+    uint64_t l = (uint64_t)(row_ptr[i + 1] - row_ptr[i]);
+    if (l >= 32) e32 += l;
+    if (l >= 512) e512 += l;
+    if (l >= 8192) e8192 += l;
+  }
+  f[27] = nnz > 0 ? (double)e32 / z : 0.0;
+  f[28] = nnz > 0 ? (double)e512 / z : 0.0;
+  f[29] = nnz > 0 ? (double)e8192 / z : 0.0;
+  uint64_t sq = 0, smax = 0;
+  int strips32 = (rows + 31) / 32;
+  for (int s = 0; s < strips32; ++s) {
+    int r1 = (s + 1) * 32 < rows ? (s + 1) * 32 : rows;
+    uint64_t ns = (uint64_t)(row_ptr[r1] - row_ptr[s * 32]);
+    sq += ns * ns;
+    if (ns > smax) smax = ns;
+  }
+  double sm = z / (double)strips32;
+  double svar = (double)sq / (double)strips32 - sm * sm;
+  if (svar < 0.0) svar = 0.0;
+  double sden = sm > 1.0 ? sm : 1.0;
+  f[30] = sqrt(svar) / sden;
+  f[31] = log2(1.0 + (double)smax / sden);
 }
 
 /* Selector network: nin -> nh (ReLU) -> nh (ReLU) -> nout, weights row-major

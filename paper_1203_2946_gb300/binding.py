@@ -49,7 +49,7 @@ class cmrs_selector(ctypes.Structure):
                 ("params", ctypes.c_void_p), ("feat_mean", ctypes.c_void_p), ("feat_scale", ctypes.c_void_p)]
 
 
-NFEAT = 24
+NFEAT = 32
 SEL_HEIGHTS = (1, 2, 4, 8, 16, 32)
 SEL_PADDED = ((32, 1), (32, 2), (16, 8))  # choices 18..20: modified CMRS (height, slots)
 SEL_CHOICES = 18 + len(SEL_PADDED)
@@ -90,6 +90,8 @@ def lib():
             "cmrs_wait_probe": ([vp, u, i, vp], i),
             "cmrs_spmv_noalloc": ([M, vp, vp, vp], i),
             "cmrs_spmv_noalloc_check": ([vp], i),
+            "cmrs_gather_probe": ([i, i, vp, vp, vp, vp, vp], i),
+            "cmrs_shard_rows": ([i, vp, i, i, vp], i),
             "cmrs_spmm": ([M, i, vp, vp, vp], i),
             "cmrs_spmm_plan_workspace": ([i, vp, vp, i, ctypes.POINTER(sz)], i),
             "cmrs_spmm_plan_create": ([i, vp, vp, vp, vp, i, i, vp, sz, vp, ctypes.POINTER(vp)], i),
@@ -314,6 +316,27 @@ def cmrs_spmv_noalloc_check(stream=None):
 def cmrs_spmv_check(A: Matrix, variant=CMRS_VARIANT_AUTO, stream=None):
     ws = A.spmv_workspace(variant)
     _check(lib().cmrs_spmv_check(A.ref(), variant, _ptr(ws), _stream(stream)), "cmrs_spmv_check")
+
+
+def cmrs_gather_probe(col, val, x, out=None, stream=None):
+    """Streams col (int32) and val (float32 or None), gathers x[col] and sums
+    the products into out (device float32 [1]): the gather floor of a matrix."""
+    if out is None:
+        out = torch.empty(1, dtype=torch.float32, device=x.device)
+    _check(lib().cmrs_gather_probe(col.numel(), x.numel(), _ptr(col), _ptr(val), _ptr(x), _ptr(out),
+                                   _stream(stream)), "cmrs_gather_probe")
+    return out
+
+
+def cmrs_shard_rows(row_ptr, height, parts):
+    """Row bounds of `parts` contiguous ranges of whole strips, balanced by
+    entries plus rows (host numpy int32 RowPtr in, numpy int32 [parts + 1])."""
+    import numpy as np
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    out = np.empty(parts + 1, dtype=np.int32)
+    _check(lib().cmrs_shard_rows(rp.size - 1, rp.ctypes.data, int(height), int(parts), out.ctypes.data),
+           "cmrs_shard_rows")
+    return out
 
 
 def cmrs_wait_probe(ws, tries, arrive, stream=None):

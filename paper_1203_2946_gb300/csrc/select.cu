@@ -13,7 +13,7 @@
 namespace cmrs {
 namespace {
 
-constexpr int kNFeat = 24;
+constexpr int kNFeat = 32;
 constexpr int kHeights[6] = {1, 2, 4, 8, 16, 32};
 // choices 18, 19, 20: the modified CMRS of Section 6.6 at (height, slots)
 constexpr int kPadChoice[3][2] = {{32, 1}, {32, 2}, {16, 8}};
@@ -22,6 +22,9 @@ struct FeatAcc {
   unsigned long long sum_l2, max_l, empty, same, near, sum_d, max_d;
   unsigned long long bins[8];
   unsigned long long spread[6], nonempty[6];
+  // modified CMRS items at (32, 1), (32, 2), (16, 8); entries in rows of
+  // >= 32, 512, 8192; sum of squares and max of 32-row strip entry counts
+  unsigned long long pad[3], elong[3], s32_sq, s32_max;
 };
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -42,13 +45,15 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 // and a segmented shuffle scan over the batch gives each row's min and max,
 // which the row's lane carries over batches.  The strips of every height
 // h = 2^e <= 32 are aligned groups of h lanes, so a shuffle tree over the
-// rows' min and max gives each strip's column spread in the same pass.  A
-// group with an invalid RowPtr range is skipped.
+// rows' min and max gives each strip's column spread in the same pass, and
+// one over the row lengths each 32- and 16-row strip's entry count and
+// longest row (the modified CMRS pass counts).  A group with an invalid
+// RowPtr range is skipped.
 constexpr int kFeatU = 4;
 __global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             FeatAcc *acc) {
-  __shared__ unsigned long long s[15], s_spread[6], s_ne[6];
-  if (threadIdx.x < 15) s[threadIdx.x] = 0;
+  __shared__ unsigned long long s[23], s_spread[6], s_ne[6];
+  if (threadIdx.x < 23) s[threadIdx.x] = 0;
   if (threadIdx.x < 6) {
     s_spread[threadIdx.x] = 0;
     s_ne[threadIdx.x] = 0;
@@ -60,6 +65,7 @@ __global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, c
   const long long groups = ((long long)rows + 31) / 32;
   unsigned long long l2 = 0, mxl = 0, empty = 0, same = 0, near = 0, sd = 0, mxd = 0;
   unsigned long long bins[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long pad1 = 0, pad2 = 0, pad8 = 0, e32 = 0, e512 = 0, e8192 = 0, ssq = 0, smx = 0;
   for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < groups; g += nw) {
     const long long r0 = g * 32, r = r0 + lane;
     const int nrows = (int)min(32LL, (long long)rows - r0);
@@ -84,6 +90,29 @@ __global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, c
         while (bb < 7 && l >= (2ull << bb)) ++bb;
 #pragma unroll
         for (int q = 0; q < 8; ++q) bins[q] += q == bb;  // registers, not a local array
+      }
+      e32 += l >= 32 ? l : 0ull;
+      e512 += l >= 512 ? l : 0ull;
+      e8192 += l >= 8192 ? l : 0ull;
+    }
+    // this group is strip g of height 32 and strips 2g, 2g+1 of height 16:
+    // entries and longest row of each, by a shuffle tree over the lanes
+    {
+      unsigned long long ns = lane < nrows ? (unsigned long long)len : 0ull, ms = ns;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        if (o == 16 && (lane & 15) == 0) {  // the 16-row strips, before their halves meet
+          const unsigned long long c = max((ns + 31) / 32, (ms + 7) / 8);
+          pad8 += 32 * c;
+        }
+        ns += __shfl_xor_sync(kAll, ns, o);
+        ms = max(ms, __shfl_xor_sync(kAll, ms, o));
+      }
+      if (lane == 0) {
+        pad1 += 32 * ms;
+        pad2 += 32 * max((ns + 31) / 32, (ms + 1) / 2);
+        ssq += ns * ns;
+        smx = max(smx, ns);
       }
     }
     // entries
@@ -164,6 +193,14 @@ __global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, c
   sd = warp_sum(sd);
   mxd = warp_max(mxd);
   for (int bb = 0; bb < 8; ++bb) bins[bb] = warp_sum(bins[bb]);
+  pad1 = warp_sum(pad1);
+  pad2 = warp_sum(pad2);
+  pad8 = warp_sum(pad8);
+  e32 = warp_sum(e32);
+  e512 = warp_sum(e512);
+  e8192 = warp_sum(e8192);
+  ssq = warp_sum(ssq);
+  smx = warp_max(smx);
   if (lane == 0) {
     atomicAdd(&s[0], l2);
     atomicMax(&s[1], mxl);
@@ -173,6 +210,14 @@ __global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, c
     atomicAdd(&s[5], sd);
     atomicMax(&s[6], mxd);
     for (int bb = 0; bb < 8; ++bb) atomicAdd(&s[7 + bb], bins[bb]);
+    atomicAdd(&s[15], pad1);
+    atomicAdd(&s[16], pad2);
+    atomicAdd(&s[17], pad8);
+    atomicAdd(&s[18], e32);
+    atomicAdd(&s[19], e512);
+    atomicAdd(&s[20], e8192);
+    atomicAdd(&s[21], ssq);
+    atomicMax(&s[22], smx);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -184,6 +229,12 @@ __global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, c
     atomicAdd(&acc->sum_d, s[5]);
     atomicMax(&acc->max_d, s[6]);
     for (int bb = 0; bb < 8; ++bb) atomicAdd(&acc->bins[bb], s[7 + bb]);
+    for (int q = 0; q < 3; ++q) {
+      atomicAdd(&acc->pad[q], s[15 + q]);
+      atomicAdd(&acc->elong[q], s[18 + q]);
+    }
+    atomicAdd(&acc->s32_sq, s[21]);
+    atomicMax(&acc->s32_max, s[22]);
   }
   if (threadIdx.x < 6) {
     atomicAdd(&acc->spread[threadIdx.x], s_spread[threadIdx.x]);
@@ -191,7 +242,7 @@ __global__ void k_feat_rows(int rows, int nnz, const int32_t *__restrict__ rp, c
   }
 }
 
-// The 24 features from the integer sums, with the same operations, in the
+// The 32 features from the integer sums, with the same operations, in the
 // same order, as their definition (no contraction into FMAs); thread t
 // computes feature t.
 __global__ void k_feat_final(int rows, int nnz, const FeatAcc *acc, double *f) {
@@ -224,9 +275,24 @@ __global__ void k_feat_final(int rows, int nnz, const FeatAcc *acc, double *f) {
     v = nnz > 0 ? __ddiv_rn((double)acc->near, z) : 0.0;
   } else if (t == 17) {
     v = rows > 1 ? __ddiv_rn((double)acc->same, (double)(rows - 1)) : 0.0;
-  } else {
+  } else if (t < 24) {
     const double ne = (double)acc->nonempty[t - 18];
     v = log2(__dadd_rn(1.0, ne > 0 ? __ddiv_rn((double)acc->spread[t - 18], ne) : 0.0));
+  } else if (t < 27) {
+    v = nnz > 0 ? log2(__ddiv_rn((double)acc->pad[t - 24], z)) : 0.0;
+  } else if (t < 30) {
+    v = nnz > 0 ? __ddiv_rn((double)acc->elong[t - 27], z) : 0.0;
+  } else {
+    const double ns = (double)((rows + 31) / 32);
+    const double sm = __ddiv_rn(z, ns);
+    const double sden = sm > 1.0 ? sm : 1.0;
+    if (t == 30) {
+      double var = __dsub_rn(__ddiv_rn((double)acc->s32_sq, ns), __dmul_rn(sm, sm));
+      if (var < 0.0) var = 0.0;
+      v = __ddiv_rn(sqrt(var), sden);
+    } else {
+      v = log2(__dadd_rn(1.0, __ddiv_rn((double)acc->s32_max, sden)));
+    }
   }
   f[t] = v;
 }

@@ -308,11 +308,11 @@ def batched_banded(spec) -> tuple:
     return a, X
 
 
-def selector_family_specs(count: int = 2000, seed: int = 11, max_nnz: int = 6_000_000):
+def selector_family_specs(count: int = 2000, seed: int = 11, max_nnz: int | None = None):
     """The selector corpus: families {stencil2d, stencil3d, banded, blockdiag,
     powerlaw, uniform}; n log-uniform in [1e4, 2e6]; target nnz/row
-    log-uniform in [2, 200] where the family lets it vary; specs whose
-    expected nnz exceeds max_nnz shrink n to fit (recorded in the spec)."""
+    log-uniform in [2, 200] where the family lets it vary (up to 4e8 entries);
+    with max_nnz set, specs whose expected nnz exceeds it shrink n to fit."""
     rng = np.random.default_rng(seed)
     fams = ["stencil2d", "stencil3d", "banded", "blockdiag", "powerlaw", "uniform"]
     specs = []
@@ -335,7 +335,7 @@ def selector_family_specs(count: int = 2000, seed: int = 11, max_nnz: int = 6_00
             s["mu"] = min(mu, 60.0 * 3)
         elif fam == "powerlaw":
             s["alpha"] = float(rng.uniform(1.8, 2.6))
-        if s["n"] * s["mu"] > max_nnz:
+        if max_nnz is not None and s["n"] * s["mu"] > max_nnz:
             s["n"] = max(10_000, int(max_nnz / s["mu"]))
         specs.append(s)
     return specs

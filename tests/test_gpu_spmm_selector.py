@@ -231,9 +231,9 @@ def test_mlp_forward_backward_adam_vs_oracle(b):
 def test_training_reduces_loss(b):
     from paper_1203_2946_gb300 import selector
     rng = np.random.default_rng(1)
-    feats = rng.normal(0, 1, (300, 24))
-    # synthetic costs with a learnable structure: the best choice depends on two features
-    w = rng.normal(0, 1, (24, selector.NCHOICE))
+    feats = rng.normal(0, 1, (300, b.NFEAT))
+    # synthetic costs with a learnable structure: the best choice depends on the features
+    w = rng.normal(0, 1, (b.NFEAT, selector.NCHOICE))
     times = np.exp(0.3 * np.tanh(feats @ w))
     idx = np.arange(300)
     model = selector.train(feats, times, idx, steps=600, batch=128, lr=3e-3)
@@ -249,8 +249,8 @@ def test_select_strip_exhaustive_and_model(b):
     rp, ci, _ = to_dev(a)
     h, v, m = b.cmrs_select_strip(rp, ci, a.cols, None)
     assert h in b.SEL_HEIGHTS and (v in (0, 1, 2) and m == 0 or (h, m) in b.SEL_PADDED and v == b.CMRS_VARIANT_PADDED)
-    model = {"params": torch.from_numpy(selector.init_params(3)).cuda(), "mean": torch.zeros(24).cuda(),
-             "scale": torch.full((24,), 0.1).cuda(), "nh": 64}
+    model = {"params": torch.from_numpy(selector.init_params(3)).cuda(), "mean": torch.zeros(b.NFEAT).cuda(),
+             "scale": torch.full((b.NFEAT,), 0.1).cuda(), "nh": 64}
     h2, v2, m2 = b.cmrs_select_strip(rp, ci, a.cols, model)
     # the device argmin agrees with the host-side prediction of the same network
     f = b.cmrs_features(rp, ci).cpu().numpy()[None, :]

@@ -356,6 +356,51 @@ def test_features_bruteforce_random(orc):
         assert f[18 + e] == pytest.approx(math.log2(1 + np.mean(sp)))
 
 
+def test_features_modified_cmrs_and_strip_sizes_laplacian(orc):
+    """f24..f31 on the 5-point 64x64 Laplacian, worked by hand: rows of 5
+    entries, 4 on a grid edge, 3 at a corner; a strip of 32 rows is half a grid
+    line (159 entries inside the grid, 127 on its first and last lines), a
+    strip of 16 rows a quarter (80 or 79; 64 or 63)."""
+    a, _ = inputs.workload_laplacian_64()
+    f = orc.features(a.row_ptr, a.col_ind)
+    # (32, 1): passes = longest row: 124 strips of 5, 4 strips of 4
+    assert f[24] == pytest.approx(math.log2(32 * (124 * 5 + 4 * 4) / 20224), abs=1e-15)
+    # (32, 2): max(ceil(159/32), ceil(5/2)) = 5 and max(ceil(127/32), 2) = 4: as (32, 1)
+    assert f[25] == f[24]
+    # (16, 8): 248 strips of ceil(80/32) = 3 passes, 8 on the first and last lines of 2
+    assert f[26] == pytest.approx(math.log2(32 * (248 * 3 + 8 * 2) / 20224), abs=1e-15)
+    assert f[27] == f[28] == f[29] == 0.0
+    # 32-row strips: 124 of 159 entries, 4 of 127; mean 158, variance 31
+    assert f[30] == pytest.approx(math.sqrt(31) / 158, rel=1e-12)
+    assert f[31] == pytest.approx(math.log2(1 + 159 / 158), rel=1e-12)
+
+
+def test_features_padded_counts_match_the_arrangement(orc):
+    """f24..f26 against the item counts of the Section 6.6 arrangement itself
+    (orc_pad_arrange, pinned on its own), on matrices with skewed rows."""
+    for seed, maker in enumerate([lambda s: inputs.powerlaw_rows(3000, 1.9, 400, seed=s),
+                                  lambda s: inputs.random_csr(700, 900, 0.02, seed=s, empty_row_frac=0.3),
+                                  lambda s: inputs.banded_random(2000, 300, 1, 90, seed=s)]):
+        a = maker(seed)
+        f = orc.features(a.row_ptr, a.col_ind)
+        for q, (h, m) in enumerate([(32, 1), (32, 2), (16, 8)]):
+            c = orc.csr_to_cmrs(a.row_ptr, a.col_ind, a.val, a.cols, h)
+            arr = orc.pad_arrange(a.rows, h, c["strip_ptr"], c["packed"], m)
+            assert f[24 + q] == pytest.approx(math.log2(int(arr["strip_ptr"][-1]) / a.nnz), abs=1e-14)
+
+
+def test_features_entry_weighted_lengths(orc):
+    lengths = [0, 5, 31, 32, 511, 512, 8191, 8192, 9000, 3]
+    a = inputs.from_lengths(lengths, 20000, seed=1)
+    f = orc.features(a.row_ptr, a.col_ind)
+    z = sum(lengths)
+    assert f[27] == pytest.approx((32 + 511 + 512 + 8191 + 8192 + 9000) / z, rel=1e-14)
+    assert f[28] == pytest.approx((512 + 8191 + 8192 + 9000) / z, rel=1e-14)
+    assert f[29] == pytest.approx((8192 + 9000) / z, rel=1e-14)
+    # one strip of 32 rows holds everything: no spread, the max is the mean
+    assert f[30] == 0.0 and f[31] == 1.0
+
+
 # ----------------------------------------------------------------------------- selector network (textbook MLP, Adam)
 def _net(rng, nin=24, nh=64, nout=18, scale=0.3):
     return dict(W1=rng.normal(0, scale, (nh, nin)), b1=rng.normal(0, 0.1, nh),

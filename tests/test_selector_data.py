@@ -20,7 +20,7 @@ def _split(n, held_out=500, seed=0):
 def test_corpus_shapes_and_report():
     d = np.load(os.path.join(DATA, "selector_corpus.npz"))
     f, t = d["features"], d["times"]
-    assert f.shape == (2000, 24) and t.shape == (2000, 21)
+    assert f.shape == (2000, 32) and t.shape == (2000, 21)
     assert np.isfinite(f).all() and (t > 0).all()
     specs = json.loads(str(d["specs"]))
     assert len(specs) == 2000 and {s["family"] for s in specs} >= {"stencil2d", "stencil3d", "banded", "blockdiag",
@@ -28,12 +28,19 @@ def test_corpus_shapes_and_report():
     rep = json.load(open(os.path.join(DATA, "selector_report.json")))
     assert rep["count"] == 2000 and rep["held_out"] == 500
     assert rep["network"]["geomean"] <= 1.10 < rep["fixed_default_h4_row"]["geomean"]
+    # the whole stated range: n from 1e4 to 2e6, 2 to 200 entries per row, no size cap
+    sizes = d["sizes"]
+    assert sizes.shape == (2000, 2) and rep["max_nnz"] is None
+    assert sizes[:, 0].min() < 12_000 and sizes[:, 0].max() > 1_900_000
+    mu = sizes[:, 1] / sizes[:, 0]
+    assert mu.min() < 2.5 and mu.max() > 190 and sizes[:, 1].max() > 300_000_000
+    assert rep["realised"]["nnz"] == [int(sizes[:, 1].min()), int(sizes[:, 1].max())]
 
 
 def test_committed_model_regret_with_oracle_forward():
     d = np.load(os.path.join(DATA, "selector_corpus.npz"))
     m = np.load(os.path.join(DATA, "selector_model.npz"))
-    nin, nh, nout = 24, int(m["nh"]), 21
+    nin, nh, nout = 32, int(m["nh"]), 21
     p = m["params"].astype(np.float64)
     sizes = [nh * nin, nh, nh * nh, nh, nout * nh, nout]
     parts = np.split(p, np.cumsum(sizes)[:-1])
