@@ -19,7 +19,7 @@ buffer pairs.
 
   python bench.py [--steps K] [--warmup W] [--height H] [--variant row|strip|merge|padded|auto] [--slots M]
   python bench.py --impl reference      # the CPU oracle on the same workload
-  torchrun --nproc-per-node N bench.py --gpus N   # N independent replicas
+  torchrun --nproc-per-node N bench.py --gpus N   # the headline split over N GPUs by strips
 """
 from __future__ import annotations
 
@@ -446,10 +446,28 @@ class L2Flush:
         torch.sum(self.r, dim=0, keepdim=True, out=self.acc)
 
 
-def time_steps(fn, steps, flush, stream):
+def time_steps(fn, steps, flush, stream, warm_steps=3, warm_s=0.05):
+    """Times `steps` steps, each {flush, fn} with fn bracketed by CUDA events
+    on `stream`.  Before them, at least `warm_steps` untimed steps of the same
+    {flush, fn} pattern, for at least `warm_s` seconds: the first product
+    after the GPU has idled (a matrix built on the host, a synchronising read)
+    measured up to twice its steady time (228.6 vs 112.6 us for the 27-point
+    headline).  The warm-up is left running on the GPU and a short spin
+    kernel follows it, so the timed steps start on a busy GPU and the host
+    enqueues them ahead of it."""
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0 = time.perf_counter()
+    i = 0
+    while i < warm_steps or time.perf_counter() - t0 < warm_s:
+        flush(i)
+        fn()
+        i += 1
+        if i % 32 == 0:
+            torch.cuda.synchronize()  # keeps the launch queue short
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(min(steps, 256) * 30e-6 * 2.0e9))  # ~30 us of GPU time per step to enqueue
     for i in range(steps):
         flush(i)
         starts[i].record(stream)
@@ -459,10 +477,73 @@ def time_steps(fn, steps, flush, stream):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
+def run_sharded(args, rank, world, dist):
+    """N > 1: the headline matrix split over the ranks by strips (one
+    contiguous range of whole strips per GPU, balanced by entries plus rows);
+    a step is the exchange of x (one NCCL broadcast per rank's piece) and the
+    rank's local product.  Total work is fixed: strong scaling."""
+    import torch
+    from paper_1203_2946_gb300 import build
+    build.build()
+    from paper_1203_2946_gb300 import binding as b, inputs, shard
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    a, x = inputs.workload_stencil27_128()
+    h = args.height
+    slots = args.slots if args.variant == "padded" else None
+    S = shard.ShardedSpmv(a, rank, world, h, dtype=b.CMRS_F64, slots=slots, device=dev)
+    S.x_local().copy_(torch.from_numpy(x[S.r0:S.r1]))
+    flush = L2Flush(dev)
+    peak, peak_kind = measured_peaks()
+    bp = beta_plus(a.nnz, a.rows, (a.rows + h - 1) // h, 8)
+    for _ in range(max(3, args.warmup)):
+        S.step()
+    sampler = ClockSampler(None)
+    barrier(dist)
+    torch.cuda.synchronize()
+    with sampler:
+        times = time_steps(S.step, args.steps, flush, stream, warm_steps=max(3, args.warmup), warm_s=0.25)
+    barrier(dist)
+    total_ms = max_over_ranks(dist, sum(times))
+    per_ms = total_ms / args.steps
+    local_ms = max_over_ranks(dist, statistics.mean(time_steps(S.product, 20, flush, stream)))
+    # e2e: this rank's piece of x in from pinned host memory, exchange, product, its rows of y out
+    xh = torch.from_numpy(np.ascontiguousarray(x[S.r0:S.r1])).pin_memory()
+    yh = torch.empty(S.rows, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        S.x_local().copy_(xh, non_blocking=True)
+        S.step()
+        yh.copy_(S.y, non_blocking=True)
+    e_ms = max_over_ranks(dist, statistics.mean(time_steps(e2e_step, 20, lambda i: None, stream)))
+    gbs = bp / (per_ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "27-point stencil 128^3 (n=%d, nnz=%d), FP64, %s, split over %d GPUs by strips"
+                                   % (a.rows, a.nnz, ("modified CMRS h=%d, M=%d" % (h, slots)) if slots else
+                                      "CMRS h=%d" % h, world),
+                       "height": h, "slots": slots, "bytes_per_step": bp, "row_bounds": [int(v) for v in S.bounds],
+                       "l2": L2_NOTE, "parallelism": "strip shards x%d, x exchanged by NCCL broadcasts" % world},
+            "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / world / peak, "peak_kind": peak_kind + " (hbm_gbs), per GPU",
+                         "traffic": None, "kernel": "k_spmv_padded" if slots else "k_spmv_row"},
+            "local_product_ms_max_over_ranks": local_ms,
+            "e2e": {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
+                    "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(yh.numel() * 8),
+                    "note": "per rank: its piece of x in, exchange, product, its rows of y out (max over ranks)"},
+            "gpu_launches": args.steps, "clocks": sampler.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def run_ours(args):
     import numpy as np
     import torch
     rank, world, dist = dist_setup(args.gpus)
+    if world > 1:
+        return run_sharded(args, rank, world, dist)
     from paper_1203_2946_gb300 import build
     build.build()
     from paper_1203_2946_gb300 import binding as b, inputs
@@ -513,7 +594,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with sampler:
-        times = time_steps(step, args.steps, flush, stream)
+        times = time_steps(step, args.steps, flush, stream, warm_steps=max(3, args.warmup), warm_s=0.25)
     barrier(dist)
     wall = time.perf_counter() - wall0
     total_ms = max_over_ranks(dist, sum(times))
@@ -550,7 +631,7 @@ def run_ours(args):
                    "slots": args.slots if args.variant == "padded" else None,
                    "stored_items_per_nnz": M.nnz / a.nnz,
                    "l2": L2_NOTE,
-                   "parallelism": "replicas x%d" % world if world > 1 else "single GPU"},
+                   "parallelism": "single GPU"},
         "gflops": 2 * a.nnz / (per_ms / 1e3) / 1e9,
         "gflops_paper": (2 * a.nnz - a.rows) / (per_ms / 1e3) / 1e9,
         "eta": eta(a.nnz, a.rows, strips, 8, per_ms, peak) if dt == b.CMRS_F64 else None,
@@ -581,6 +662,15 @@ def run_ours(args):
         line["selector"] = selector_cost(b, a, rp, ci)
         line["conversion"] = conversion_times(b, a, rp, ci, va, M_csr, h,
                                               args.slots if args.variant == "padded" else None)
+        # the other workloads, each with its own beta+ roofline
+        import oracle
+        pl = powerlaw_block(b, inputs, oracle, dev, flush, stream, 100, args.warmup)
+        pl.pop("_keep")
+        line["powerlaw"] = pl
+        bt = batched_block(b, inputs, oracle, dev, flush, stream, 20, args.warmup, 4, 256)
+        line["batched"] = {"ms": bt["ms"], "gbs": bt["gbs"], "config": bt["config"], "roofline": bt["roofline"],
+                           "e2e": bt["e2e"], **bt["extra"]}
+        line["selector_sample"] = selector_sample(b, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(a, x, strips)
         line["cpu_baseline_all_cores"] = cpu_oracle_rate_all_cores(a, x, strips)
@@ -723,6 +813,34 @@ def selector_cost(b, a, rp, ci, reps=5):
     return {"ms": statistics.median(ts[1:]) * 1e3, "choice": name}
 
 
+def selector_sample(b, dev, count=24, seed=5):
+    """The committed selector on `count` of its 500 held-out corpus matrices
+    (seeded choice), each regenerated on the device and timed again by the
+    exhaustive sweep here: regret t(network's choice) / t(best), against the
+    fixed default h = 4, ROW."""
+    from paper_1203_2946_gb300 import corpus, inputs, selector
+    model = selector.load_model(os.path.join(ROOT, "paper_1203_2946_gb300", "data", "selector_model.npz"))
+    specs = inputs.selector_family_specs(2000, seed=11)
+    _, held = selector.split(len(specs), 500, seed=0)
+    pick = np.random.default_rng(seed).choice(held, count, replace=False)
+    timer = selector.Timer(dev)
+    net, default, names, sizes = [], [], [], []
+    for i in pick:
+        rows, cols, rp, ci, va = corpus.device_matrix(specs[i], dev)
+        _, t = selector.time_all_choices(rows, cols, rp, ci, va, timer)
+        h, v, m = b.cmrs_select_strip(rp, ci, cols, model)
+        c = 18 + b.SEL_PADDED.index((h, m)) if v == b.CMRS_VARIANT_PADDED else 3 * b.SEL_HEIGHTS.index(h) + v
+        net.append(t[c] / t.min())
+        default.append(t[3 * b.SEL_HEIGHTS.index(4)] / t.min())
+        names.append(selector.choice_name(c))
+        sizes.append(int(ci.numel()))
+    geo = lambda r: float(np.exp(np.mean(np.log(r))))  # noqa: E731
+    return {"matrices": count, "nnz_range": [min(sizes), max(sizes)], "network_regret_geomean": geo(net),
+            "network_within_10pct": float(np.mean(np.array(net) <= 1.10)), "network_regret_max": float(max(net)),
+            "fixed_default_h4_row_geomean": geo(default),
+            "note": "held-out corpus matrices regenerated and timed again in this run (21 choices, L2 flushed)"}
+
+
 def sorted_strips(b, a, xd, rp, ci, va, flush, stream, steps=60):
     """Section 4's fourth optimisation: the STRIP kernel (Algorithm 1) on
     unsorted strips and on strips stably sorted by column, at heights 4 and 16
@@ -761,6 +879,8 @@ def main():
         run_ours(args)
     elif args.workload == "irregular":
         run_irregular(args)
+    elif args.workload == "powerlaw":
+        run_powerlaw(args)
     else:
         run_secondary(args)
 
@@ -789,7 +909,7 @@ def run_secondary(args):
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(None)
     steps = args.steps
-    if args.workload in ("powerlaw", "laplacian", "p7", "dense4"):
+    if args.workload in ("laplacian", "p7", "dense4"):
         if args.workload == "p7":
             a = inputs.permutation_matrix()
             x = inputs.uniform_vector(a.cols, 0)
@@ -800,11 +920,6 @@ def run_secondary(args):
             x = inputs.uniform_vector(a.cols, 0)
             dt, sv, name = b.CMRS_F64, 8, "f64"
             wl = "dense4: 10^4 x 10^4 dense matrix stored as sparse (nnz = 10^8), FP64"
-        elif args.workload == "powerlaw":
-            a, x = inputs.workload_powerlaw_4m()
-            dt, sv, name = b.CMRS_F32, 4, "f32"
-            wl = ("power-law rows, Zipf(2.1) clipped to [1,100000], n=4194304, nnz=%d (mean %.2f), "
-                  "FP32 values and x" % (a.nnz, a.nnz / a.rows))
         else:
             a, x = inputs.workload_laplacian_64()
             dt, sv, name = b.CMRS_F64, 8, "f64"
@@ -824,7 +939,7 @@ def run_secondary(args):
             fn()
         torch.cuda.synchronize()
         with sampler:
-            times = time_steps(fn, steps, flush, stream)
+            times = time_steps(fn, steps, flush, stream, warm_steps=max(3, args.warmup), warm_s=0.25)
         per_ms = statistics.mean(times)
         S = (a.rows + h - 1) // h
         bp = beta_plus(a.nnz, a.rows, S, sv)
@@ -838,6 +953,8 @@ def run_secondary(args):
             extra["cpu_baseline"] = cpu_oracle_rate(inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind,
                                                                a.val.astype(np.float64)), x.astype(np.float64), S)
         extra["stored_items_per_nnz"] = M.nnz / max(a.nnz, 1)
+        if args.workload == "p7":
+            extra["gather_floor"] = gather_floor(b, ci, None, xd.float(), flush, stream, per_ms)
         if args.workload in ("p7", "dense4"):
             var = {}
             for vn, vv in b.VARIANTS.items():  # plain CMRS at the same height
@@ -861,28 +978,6 @@ def run_secondary(args):
                     del Q
                 extra["padded_forms_f64"] = pads
             fn()
-        if args.workload == "powerlaw":
-            forms = {}
-            for fname, fdt, fbp in (("bf16", b.CMRS_BF16, 6 * a.nnz + 4 * S + 8 * a.rows),):
-                F = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=fdt)
-                fws = F.spmv_workspace(v)
-                ff = lambda: b.cmrs_spmv(F, xd, yd, v, fws)  # noqa: E731
-                for _ in range(3):
-                    ff()
-                fms = statistics.mean(time_steps(ff, min(steps, 200), flush, stream))
-                frel = np.abs(yd.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
-                forms[fname] = {"gbs": fbp / (fms / 1e3) / 1e9, "ms": fms, "speedup_vs_f32": per_ms / fms,
-                                "err_vs_f64_oracle": {"max": float(frel.max()), "median": float(np.median(frel))}}
-            extra["forms"] = forms
-            var = {}
-            for vn, vv in b.VARIANTS.items():
-                vws = M.spmv_workspace(vv)
-                g = lambda: b.cmrs_spmv(M, xd, yd, vv, vws)  # noqa: E731
-                for _ in range(2):
-                    g()
-                vms = statistics.mean(time_steps(g, 20, flush, stream))
-                var[vn] = {"ms": vms, "gbs": bp / (vms / 1e3) / 1e9}
-            extra["variants_f32"] = var
         xh = torch.from_numpy(x).pin_memory()
         yhs = [torch.empty(a.rows, dtype=xd.dtype).pin_memory() for _ in range(2)]
         e_ms = e2e_pipelined(lambda xv, yv: b.cmrs_spmv(M, xv, yv, v, ws), xh, [xd, torch.empty_like(xd)],
@@ -906,11 +1001,25 @@ def run_secondary(args):
         return
 
     # ---- batched: 256 banded-random matrices, k right-hand sides each
-    specs = inputs.batched_banded_specs()[:args.batch_count]
+    r = batched_block(b, inputs, oracle, dev, flush, stream, steps, args.warmup, args.height, args.batch_count,
+                      sampler)
+    line = _line(args, r["gbs"], "GB/s", r["ms"], "f32", r["config"], r["roofline"], r["e2e"], r["gpu_launches"],
+                 sampler.summary(), r["extra"])
+    print(json.dumps(line), flush=True)
+
+
+def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, h, count, sampler=None):
+    """The batched workload: `count` banded-random matrices with k right-hand
+    sides each, one persistent graph-replayed launch per step (autotuned work
+    units), against per-matrix launches and per-column plain FP64 SpMV; a
+    parity sample against the oracle; e2e with X in and Y out every step."""
+    import contextlib
+    import torch
+    specs = inputs.batched_banded_specs()[:count]
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
         mats_host = pool.map(_gen_batched, specs, chunksize=4)
-    h = args.height
+    peak, peak_kind = measured_peaks()
     mats, Xs, Ys, bp, nnz_total, rows_total = [], [], [], 0, 0, 0
     for (rp_, ci_, val_, X_), sp_ in zip(mats_host, specs):
         n = rp_.size - 1
@@ -927,11 +1036,11 @@ def run_secondary(args):
     best, _ = b.cmrs_spmm_autotune(mats, Xs, Ys, candidates=(2048, 8192, 32768, 131072), reps=3)
     plan = b.SpmmPlan(mats, Xs, Ys, work_target=best, use_graph=True)
     fn = lambda: b.cmrs_spmm_batched(plan)  # noqa: E731
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         fn()
     torch.cuda.synchronize()
-    with sampler:
-        times = time_steps(fn, steps, flush, stream)
+    with (sampler if sampler is not None else contextlib.nullcontext()):
+        times = time_steps(fn, steps, flush, stream, warm_steps=max(3, warmup), warm_s=0.25)
     per_ms = statistics.mean(times)
     gbs = bp / (per_ms / 1e3) / 1e9
     # per-matrix plain launches of the same kernel, no graph
@@ -991,25 +1100,125 @@ def run_secondary(args):
         Yh[s].copy_(dsets[s][1][0], non_blocking=True)
     e_ms = e2e_pipelined_sets(lambda s: b.cmrs_spmm_batched(plans[s]), copy_in, copy_out, 10, warm=2)
     info = plan.info()
-    line = _line(args, gbs, "GB/s", per_ms, "f32",
-                 {"workload": "%d banded-random matrices (n~U[1000,200000], bandwidth~U[64,2048], 10-60 nnz/row, "
-                              "k in {1,4,8,32}), FP32, CMRS h=%d; one persistent graph-replayed launch" % (len(specs), h),
-                  "matrices": len(specs), "rows_total": rows_total, "entry_columns": nnz_total,
-                  "bytes_per_step": bp, "schedule": {"work_target": best, **info},
-                  "l2": L2_NOTE},
-                 {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                  "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmm_queue"},
-                 {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s",
-                  "h2d_bytes_per_step": int(Xh.numel() * 4), "d2h_bytes_per_step": int(Yh[0].numel() * 4),
-                  "ms_per_step": e_ms, "note": "X in and Y out in one copy each per step (every matrix's block "
-                  "at a 256-byte boundary of one buffer), two buffer sets, copies of neighbouring steps overlap"},
-                 steps, sampler.summary(),
-                 {"gflops": 2 * nnz_total / (per_ms / 1e3) / 1e9,
-                  "per_matrix_launches": {"ms": plain_ms, "speedup_of_batched": plain_ms / per_ms},
-                  "plain_f64_spmv_per_column": {"matrices": len(sub), "ms": f64_sub_ms,
-                                                "batched_f32_ms_same_subset": plain_sub_ms,
-                                                "speedup_of_f32_spmm": f64_sub_ms / plain_sub_ms},
-                  "parity_sample": {"matrices": 8, "max_err_over_tolerance": worst}})
+    return {"ms": per_ms, "gbs": gbs,
+            "config": {"workload": "%d banded-random matrices (n~U[1000,200000], bandwidth~U[64,2048], 10-60 nnz/row, "
+                                   "k in {1,4,8,32}), FP32, CMRS h=%d; one persistent graph-replayed launch"
+                                   % (len(specs), h),
+                       "matrices": len(specs), "rows_total": rows_total, "entry_columns": nnz_total,
+                       "bytes_per_step": bp, "schedule": {"work_target": best, **info}, "l2": L2_NOTE},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmm_queue"},
+            "e2e": {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": int(Xh.numel() * 4), "d2h_bytes_per_step": int(Yh[0].numel() * 4),
+                    "ms_per_step": e_ms, "note": "X in and Y out in one copy each per step (every matrix's block "
+                    "at a 256-byte boundary of one buffer), two buffer sets, copies of neighbouring steps overlap"},
+            "gpu_launches": steps,
+            "extra": {"gflops": 2 * nnz_total / (per_ms / 1e3) / 1e9,
+                      "per_matrix_launches": {"ms": plain_ms, "speedup_of_batched": plain_ms / per_ms},
+                      "plain_f64_spmv_per_column": {"matrices": len(sub), "ms": f64_sub_ms,
+                                                    "batched_f32_ms_same_subset": plain_sub_ms,
+                                                    "speedup_of_f32_spmm": f64_sub_ms / plain_sub_ms},
+                      "parity_sample": {"matrices": 8, "max_err_over_tolerance": worst}}}
+
+
+def gather_floor(b, ci, va, x32, flush, stream, kernel_ms, steps=50):
+    """k_gather_dot on the matrix's own column array (and FP32 values, if
+    given): the time any SpMV kernel pays for the streams and the x gathers
+    alone, with the row structure taken away; and the kernel's distance to it."""
+    import torch
+    out = torch.empty(1, dtype=torch.float32, device=x32.device)
+    fn = lambda: b.cmrs_gather_probe(ci, va, x32, out)  # noqa: E731
+    ms = statistics.mean(time_steps(fn, steps, flush, stream))
+    return {"ms": ms, "kernel": "k_gather_dot", "streams": "columns" + (" and FP32 values" if va is not None else ""),
+            "kernel_frac_of_floor": ms / kernel_ms,
+            "note": "floor = one pass over the streams with every x gather, no row bounds, sums or y"}
+
+
+def powerlaw_block(b, inputs, oracle, dev, flush, stream, steps, warmup, h=32, sampler=None, forms=True):
+    """Power-law rows, n = 4,194,304 (Zipf(2.1) clipped to [1, 100000]), FP32
+    values and x, MERGE at height h: time, beta+ GB/s, error against the FP64
+    oracle, the gather floor, and the BF16 form."""
+    import contextlib
+    import torch
+    peak, peak_kind = measured_peaks()
+    a, x = inputs.workload_powerlaw_4m()
+    rp, ci = torch.from_numpy(a.row_ptr).to(dev), torch.from_numpy(a.col_ind).to(dev)
+    va = torch.from_numpy(np.ascontiguousarray(a.val)).to(dev)
+    M = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_F32)
+    v = b.CMRS_VARIANT_MERGE
+    xd = torch.from_numpy(x).to(dev)
+    yd = torch.empty(a.rows, dtype=torch.float32, device=dev)
+    ws = M.spmv_workspace(v)
+    fn = lambda: b.cmrs_spmv(M, xd, yd, v, ws)  # noqa: E731
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    with (sampler if sampler is not None else contextlib.nullcontext()):
+        times = time_steps(fn, steps, flush, stream, warm_steps=max(3, warmup), warm_s=0.25)
+    ms = statistics.mean(times)
+    S = (a.rows + h - 1) // h
+    bp = beta_plus(a.nnz, a.rows, S, 4)
+    gbs = bp / (ms / 1e3) / 1e9
+    yref, scale = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val.astype(np.float64), x.astype(np.float64))
+    rel = np.abs(yd.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
+    out = {"workload": "power-law rows, Zipf(2.1) clipped to [1,100000], n=%d, nnz=%d (mean %.2f), FP32 values and "
+                       "x, CMRS h=%d, MERGE" % (a.rows, a.nnz, a.nnz / a.rows, h),
+           "ms": ms, "gbs": gbs, "bytes_per_step": bp, "gflops": 2 * a.nnz / (ms / 1e3) / 1e9,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "peak_kind": peak_kind + " (hbm_gbs)", "kernel": "k_spmv_merge",
+                        "traffic": traffic_record("k_spmv_merge", "powerlaw_f32_h%d" % h)},
+           "eta": eta(a.nnz, a.rows, S, 4, ms, peak),
+           "err_vs_f64_oracle": {"max": float(rel.max()), "median": float(np.median(rel))},
+           "gather_floor": gather_floor(b, ci, va, xd, flush, stream, ms)}
+    if forms:
+        F = b.cmrs_from_csr(rp, ci, va, a.cols, h, dtype=b.CMRS_BF16)
+        fws = F.spmv_workspace(v)
+        ff = lambda: b.cmrs_spmv(F, xd, yd, v, fws)  # noqa: E731
+        fms = statistics.mean(time_steps(ff, min(steps, 200), flush, stream))
+        frel = np.abs(yd.cpu().numpy().astype(np.float64) - yref) / np.where(scale > 0, scale, 1)
+        fbp = 6 * a.nnz + 4 * S + 8 * a.rows
+        out["forms"] = {"bf16": {"gbs": fbp / (fms / 1e3) / 1e9, "ms": fms, "speedup_vs_f32": ms / fms,
+                                 "bytes_per_step": fbp,
+                                 "err_vs_f64_oracle": {"max": float(frel.max()), "median": float(np.median(frel))}}}
+    out["_keep"] = (a, x, M, xd, yd, ws, S)
+    return out
+
+
+def run_powerlaw(args):
+    import torch
+    from paper_1203_2946_gb300 import build
+    build.build()
+    from paper_1203_2946_gb300 import binding as b, inputs
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = L2Flush(dev)
+    sampler = ClockSampler(None)
+    r = powerlaw_block(b, inputs, oracle, dev, flush, stream, args.steps, args.warmup, args.height, sampler)
+    a, x, M, xd, yd, ws, S = r.pop("_keep")
+    v = b.CMRS_VARIANT_MERGE
+    var = {}
+    for vn, vv in b.VARIANTS.items():
+        vws = M.spmv_workspace(vv)
+        g = lambda: b.cmrs_spmv(M, xd, yd, vv, vws)  # noqa: E731
+        vms = statistics.mean(time_steps(g, 20, flush, stream))
+        var[vn] = {"ms": vms, "gbs": r["bytes_per_step"] / (vms / 1e3) / 1e9}
+    xh = torch.from_numpy(x).pin_memory()
+    yhs = [torch.empty(a.rows, dtype=torch.float32).pin_memory() for _ in range(2)]
+    e_ms = e2e_pipelined(lambda xv, yv: b.cmrs_spmv(M, xv, yv, v, ws), xh, [xd, torch.empty_like(xd)],
+                         [yd, torch.empty_like(yd)], yhs, max(20, min(args.steps, 200)))
+    extra = {k: r[k] for k in ("gflops", "eta", "err_vs_f64_oracle", "gather_floor", "forms")}
+    extra["variants_f32"] = var
+    if not args.no_cpu:
+        extra["cpu_baseline"] = cpu_oracle_rate(inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind,
+                                                           a.val.astype(np.float64)), x.astype(np.float64), S)
+    line = _line(args, r["gbs"], "GB/s", r["ms"], "f32",
+                 {"workload": r["workload"], "height": args.height, "variant": "merge", "kernel_variant": "merge",
+                  "bytes_per_step": r["bytes_per_step"], "l2": L2_NOTE},
+                 r["roofline"],
+                 {"value": r["bytes_per_step"] / (e_ms / 1e3) / 1e9, "unit": "GB/s",
+                  "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(a.rows * 4), "ms_per_step": e_ms},
+                 args.steps * 3, sampler.summary(), extra)
     print(json.dumps(line), flush=True)
 
 
@@ -1068,7 +1277,7 @@ def run_irregular(args):
         fn()
     torch.cuda.synchronize()
     with sampler:
-        times = time_steps(fn, steps, flush, stream)
+        times = time_steps(fn, steps, flush, stream, warm_steps=max(3, args.warmup), warm_s=0.25)
     per_ms = statistics.mean(times)
     gbs = bp / (per_ms / 1e3) / 1e9
     yref, scale = oracle.csr_spmv(a.row_ptr, a.col_ind, a.val, x)

@@ -43,6 +43,28 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 int sm_count();  // multiprocessors of the current device (cached per device)
 
+// Programmatic dependent launch: `kernel` may begin while the kernel before
+// it in the stream is still running, once every block of that kernel has
+// executed pdl_launch_dependents() (or exited).  The kernel launched this way
+// must call pdl_wait() before it touches anything the earlier kernel writes;
+// what it does before (issuing copies of read-only inputs, say) overlaps the
+// earlier kernel's tail and the launch gap.
+template <typename... KArgs, typename... Args>
+int launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+               Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return set_cuda_error(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
 // Status word bits written by kernels (device side) and read by the host.
 enum : uint32_t {
   ST_BAD_ROWPTR = 1u,
@@ -53,6 +75,10 @@ enum : uint32_t {
 };
 
 // ------------------------------------------------------------------ device side
+// The two halves of a programmatic dependent launch (see launch_pdl).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

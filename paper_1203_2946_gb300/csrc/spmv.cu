@@ -585,6 +585,7 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
 // goes to a tile record that a fix-up kernel joins in tile order.  Rows with
 // no entries are written as 0 by the thread owning the entry before the gap.
 __global__ void k_tile_map(int strips, const int32_t *__restrict__ sp, int ntiles, int32_t *__restrict__ tile_strip) {
+  pdl_launch_dependents();  // the product may start staging its first tiles
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= strips) return;
   const long long a = sp[s], b = sp[s + 1];
@@ -629,7 +630,9 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
     issue_stage<DT>(ta, tb, nnz, packed, hi, lo, smem + st * stage_bytes, kMergeTile, &bars[st], pol, &info[st]);
   };
   int t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t, 0);
+  if (tid == 0 && t < ntiles) issue(t, 0);  // the matrix streams are inputs: no wait needed
+  pdl_wait();                                // tile_strip is k_tile_map's output
+  pdl_launch_dependents();                   // the fix-up kernel may launch and wait in turn
   for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
     const int st = it & 1;
     if (tid == 0) {
@@ -867,6 +870,7 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
 
 template <typename A>
 __global__ void k_merge_fixup(int ntiles, int rows, const TileRec *__restrict__ recs, A *__restrict__ y) {
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntiles || recs[t].tail_flag != 1) return;
   A sum = (A)recs[t].tail_sum;
@@ -897,6 +901,7 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_SPLIT_MINB) k_spmv_pa
     const typename Form<DT>::Acc *__restrict__ x, typename Form<DT>::Acc *__restrict__ part) {
   typedef typename Form<DT>::Acc A;
   extern __shared__ __align__(16) char smem[];
+  pdl_launch_dependents();  // k_pad_combine may launch; it waits for this grid's sums
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   A *buf = reinterpret_cast<A *>(smem) + (size_t)w * kM * height;
   const uint32_t mask = (1u << bits) - 1;
@@ -969,6 +974,7 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_SPLIT_MINB) k_spmv_pa
 template <typename A>
 __global__ void k_pad_combine(int rows, int height, int P, const A *__restrict__ part, A *__restrict__ y,
                               const int32_t *__restrict__ row_map) {
+  pdl_wait();
   const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= rows) return;
   const long long s = row / height, r = row - s * height;
@@ -1212,8 +1218,9 @@ int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, con
     k_spmv_padded_split<DT, kM><<<grid, kPadWarps * 32, per_h * A->height, st>>>(
         A->height, A->bits, A->strips, P, A->strip_ptr, A->col_packed, hi, lo, x, part);
     CMRS_LAUNCH_CHECK();
-    k_pad_combine<Acc><<<(int)ceil_div(A->rows, 256), 256, 0, st>>>(A->rows, A->height, P, part, y, row_map);
-    CMRS_LAUNCH_CHECK();
+    const int rc = launch_pdl(k_pad_combine<Acc>, (unsigned)ceil_div(A->rows, 256), 256, 0, st, A->rows, A->height, P,
+                              part, y, row_map);
+    if (rc) return rc;
     return CMRS_OK;
   }
   const bool aligned = ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(hi) |
@@ -1298,11 +1305,11 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
     const size_t smem = kStages * Stage<DT>::bytes(kMergeTile);
     const int per_sm = occupancy(k_spmv_merge<DT>, kMergeThreads, smem, occ);
     const int grid = (int)std::min<long long>(ntiles, (long long)per_sm * sms);
-    k_spmv_merge<DT><<<grid, kMergeThreads, smem, st>>>(A->rows, A->height, A->bits, A->strips, A->nnz, A->strip_ptr,
-                                                        A->col_packed, hi, lo, x, y, tile_strip, ntiles, recs, status);
-    CMRS_LAUNCH_CHECK();
-    k_merge_fixup<Acc><<<(int)ceil_div(ntiles, 256), 256, 0, st>>>(ntiles, A->rows, recs, y);
-    CMRS_LAUNCH_CHECK();
+    int rc = launch_pdl(k_spmv_merge<DT>, (unsigned)grid, kMergeThreads, smem, st, A->rows, A->height, A->bits,
+                        A->strips, A->nnz, A->strip_ptr, A->col_packed, hi, lo, x, y, tile_strip, ntiles, recs, status);
+    if (rc) return rc;
+    rc = launch_pdl(k_merge_fixup<Acc>, (unsigned)ceil_div(ntiles, 256), 256, 0, st, ntiles, A->rows, recs, y);
+    if (rc) return rc;
   }
   return CMRS_OK;
 }
