@@ -34,7 +34,15 @@ constexpr int kRowCap = 32 * CMRS_ROW_ROWS;   // ROW: entries per shared-memory 
 #define CMRS_MERGE_MINB_F32 5
 #endif
 constexpr int kMergeThreads = 128;
-constexpr int kMergeE = 15;  // MERGE: entries per thread; odd, so that a warp's shared loads hit 32 banks
+#ifndef CMRS_MERGE_E
+#define CMRS_MERGE_E 15
+#endif
+#ifndef CMRS_MERGE_VSMEM
+#define CMRS_MERGE_VSMEM 0
+#endif
+constexpr int kMergeE = CMRS_MERGE_E;  // MERGE: entries per thread; odd, so that a warp's shared loads hit 32 banks
+// MERGE: values read from the staged tile at their multiply-add instead of held in registers
+constexpr bool kMergeVSmem = CMRS_MERGE_VSMEM != 0;
 constexpr int kMergeTile = kMergeThreads * kMergeE;
 constexpr int kMergeWarps = kMergeThreads / 32;
 constexpr int kStripWarps = 8;
@@ -349,6 +357,118 @@ __global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
     if (!ok) break;
+  }
+}
+
+// ============================================================== LANE mapping
+// Plain CMRS, a lane per row (used by CMRS_VARIANT_ROW when the strip height
+// divides 32).  A warp takes 32 consecutive rows, i.e. whole strips, whose
+// entries are one contiguous range of the streams; one lane bulk-copies the
+// range into the warp's own shared-memory stage, and lane r then walks row r
+// with one multiply-add per entry, the row's sum in a register, as the M = 1
+// walk of Section 6.6 does on padded strips -- but on the plain layout: the
+// row starts come from one binary search on RowInStrip per lane, and the
+// stage turns the row-by-row order of the strips into the lane-by-lane order
+// of the walk.  In a warp the lanes gather x at the same position of 32
+// consecutive rows (for a stencil, consecutive columns).  No join adds (on
+// this GPU an FP64 warp instruction costs its issue slot whatever its active
+// lanes do) and no CTA barrier: each warp waits on its own mbarrier.  A range
+// longer than the stage is read from global memory instead: ROW takes this
+// mapping only for matrices whose mean row is short enough for most units to
+// fit the stage (longer rows go to the share-per-thread kernel below).
+#ifndef CMRS_ROW_LANE
+#define CMRS_ROW_LANE 1  // 0: ROW always runs k_spmv_row
+#endif
+#ifndef CMRS_LANE_CAP
+#define CMRS_LANE_CAP 896  // most entries per warp stage (28 per row)
+#endif
+#ifndef CMRS_LANE_SLACK
+#define CMRS_LANE_SLACK 40  // stage entries per row of the mean length, in 32nds (40: 1.25x)
+#endif
+#ifndef CMRS_LANE_MAX_MU
+#define CMRS_LANE_MAX_MU 28.0  // mean entries per row up to which ROW takes the lane mapping
+#endif
+#ifndef CMRS_LANE_WARPS
+#define CMRS_LANE_WARPS 4
+#endif
+#ifndef CMRS_LANE_CH_F64
+#define CMRS_LANE_CH_F64 5
+#endif
+#ifndef CMRS_LANE_CH_F32
+#define CMRS_LANE_CH_F32 16
+#endif
+constexpr int kLaneCap = CMRS_LANE_CAP;
+constexpr int kLaneWarps = CMRS_LANE_WARPS;
+
+template <int DT>
+__global__ void __launch_bounds__(kLaneWarps * 32) k_spmv_lane(int rows, int height, int bits, int cap, int nnz,
+                                                              const int32_t *__restrict__ sp,
+                                                              const uint32_t *__restrict__ packed,
+                                                              const typename Form<DT>::Stored *__restrict__ hi,
+                                                              const typename Form<DT>::Stored *__restrict__ lo,
+                                                              const typename Form<DT>::Acc *__restrict__ x,
+                                                              typename Form<DT>::Acc *__restrict__ y,
+                                                              const int32_t *__restrict__ row_map, uint32_t *status) {
+  typedef typename Form<DT>::Stored S;
+  typedef typename Form<DT>::Acc A;
+  constexpr int CH = DT == CMRS_F64 ? CMRS_LANE_CH_F64 : CMRS_LANE_CH_F32;
+  extern __shared__ __align__(128) char smem[];
+  __shared__ uint64_t bars[kLaneWarps];
+  __shared__ StageInfo info[kLaneWarps];
+  const unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  char *stg = smem + (size_t)w * Stage<DT>::bytes(cap);
+  const uint32_t mask = (1u << bits) - 1;
+  if (lane == 0) {
+    mbar_init(&bars[w], 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  uint64_t pol = 0;
+  if (lane == 0) pol = policy_evict_first();
+  const long long units = ((long long)rows + 31) / 32;
+  const long long nw = (long long)gridDim.x * kLaneWarps;
+  uint32_t phase = 0;
+  for (long long u = (long long)blockIdx.x * kLaneWarps + w; u < units; u += nw) {
+    const long long r0 = u * 32;
+    const long long r1 = min(r0 + 32, (long long)rows);
+    const int s0 = (int)(r0 / height), s1 = (int)((r1 - 1) / height) + 1;  // the unit's strips
+    const int ea = sp[s0], eb = sp[s1];
+    const bool staged = eb - ea <= cap;  // warp-uniform
+    if (staged && lane == 0) issue_stage<DT>(ea, eb, nnz, packed, hi, lo, stg, cap, &bars[w], pol, &info[w]);
+    // this lane's row and its strip's bounds, loaded while the copy is in flight
+    const long long row = r0 + lane;
+    const bool active = row < rows;
+    const int s = active ? (int)(row / height) : s0;
+    const uint32_t rr = active ? (uint32_t)(row - (long long)s * height) : 0;
+    const int sa = active ? sp[s] : 0, sb = active ? sp[s + 1] : 0;
+    bool ok = true;
+    if (staged) {
+      ok = __all_sync(kAll, mbar_wait_bounded(&bars[w], phase));
+      phase ^= 1;
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+    const uint32_t *cp = staged ? reinterpret_cast<const uint32_t *>(stg) : packed;
+    const S *vh = staged ? reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(cap)) : hi;
+    const S *vl = staged ? reinterpret_cast<const S *>(stg + Stage<DT>::colp_bytes(cap) + Stage<DT>::val_bytes(cap))
+                         : (Stage<DT>::kSplit ? lo : hi);
+    const long long base = staged ? info[w].a8 : 0;
+    // row r ends where row r + 1 starts, or at its strip's end (the height
+    // divides 32, so lane 31's row is the last of its strip)
+    int k0 = sa;
+    if (active && rr > 0) k0 = lb_ris(cp, base, sa, sb, rr, mask);
+    const int nxt = __shfl_down_sync(kAll, k0, 1);
+    int k1 = (rr + 1 == (uint32_t)height || row + 1 >= rows || lane == 31) ? sb : nxt;
+    if (!active) k0 = k1 = 0;
+    const A acc = seg_dot<DT, CH, 1>(cp, vh, vl, base, k0, k1, bits, x);
+    if (active) {
+      const long long t = row_map ? row_map[row] : row;  // y position (row map of a reordered matrix)
+      if (t >= 0 && t < rows) y[t] = acc;
+    }
+    __syncwarp();  // every lane is done with the stage before the next copy lands in it
   }
 }
 
@@ -691,7 +811,7 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
           if (decltype(full)::value || j < n) {
             const long long i = k0 + j - base;
             c[j] = cp[i];
-            v[j] = Form<DT>::value(vh, vl, i);
+            if (!kMergeVSmem) v[j] = Form<DT>::value(vh, vl, i);
             xv[j] = ld_x(x + (c[j] >> bits));
           }
         }
@@ -720,7 +840,8 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
       // the warp reconverged first, so that every FMA issues for the whole
       // warp (FP64 issue is charged per warp instruction).
       __syncwarp(part);
-      A acc = fma_acc(v[0], xv[0], A(0));
+      auto val_of = [&](int j) -> A { return kMergeVSmem ? Form<DT>::value(vh, vl, k0 + j - base) : v[j]; };
+      A acc = fma_acc(val_of(0), xv[0], A(0));
       A head_sum = A(0);
       bool first = true;  // the current run is this thread's first
       uint32_t run_row = rw[0];
@@ -734,7 +855,7 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
             if (nw && !to_head && rw[j - 1] < (uint32_t)rows) y[rw[j - 1]] = acc;
             first = first && !nw;
             acc = nw ? A(0) : acc;
-            acc = fma_acc(v[j], xv[j], acc);
+            acc = fma_acc(val_of(j), xv[j], acc);
             run_row = rw[j];
           }
         }
@@ -1270,7 +1391,23 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
   Acc *y = reinterpret_cast<Acc *>(yv);
   uint32_t *status = reinterpret_cast<uint32_t *>(ws);
   const int sms = sm_count();
-  if (variant == CMRS_VARIANT_ROW) {
+  if (variant == CMRS_VARIANT_ROW && CMRS_ROW_LANE && 32 % A->height == 0 &&
+      (double)A->nnz <= CMRS_LANE_MAX_MU * A->rows) {
+    // stage: 1.25x the entries of an average 32 rows, in multiples of 32, at
+    // most kLaneCap -- short rows leave shared memory for more warps; a
+    // longer unit is read from global memory
+    static Occ occ[kLaneCap / 32 + 1];
+    const double mu = A->rows > 0 ? (double)A->nnz / A->rows : 0.0;
+    const int cap = (int)std::min<long long>(kLaneCap, std::max<long long>(128, ceil_div((long long)(CMRS_LANE_SLACK * mu), 32) * 32));
+    const size_t smem = (size_t)kLaneWarps * Stage<DT>::bytes(cap);
+    const int per_sm = occupancy(k_spmv_lane<DT>, kLaneWarps * 32, smem, occ[cap / 32],
+                                 (size_t)kLaneWarps * Stage<DT>::bytes(kLaneCap));
+    const long long need = ceil_div(ceil_div(A->rows, 32), kLaneWarps);
+    const int grid = (int)std::min<long long>(need, (long long)per_sm * sms);
+    k_spmv_lane<DT><<<grid, kLaneWarps * 32, smem, st>>>(A->rows, A->height, A->bits, cap, A->nnz, A->strip_ptr,
+                                                          A->col_packed, hi, lo, x, y, row_map, status);
+    CMRS_LAUNCH_CHECK();
+  } else if (variant == CMRS_VARIANT_ROW) {
     static Occ occ;
     const size_t smem = kRowStages * Stage<DT>::bytes(kRowCap);
     const int per_sm = occupancy(k_spmv_row<DT>, RowCfg<DT>::kThreads, smem, occ);

@@ -212,6 +212,20 @@ def test_spmv_skewed_rows(b, dtype):
             check_spmv(b, M, a, x, var, dtype)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_spmv_row_lane_long_units(b, dtype):
+    """ROW at heights dividing 32 gives a lane per row: 32 rows of 40..60
+    entries pass through the warp's stage in chunks, and rows of 1..8 entries
+    (with a tail that is not a multiple of 32) in one copy each."""
+    long_rows = inputs.banded_random(20_003, 900, 40, 60, seed=5)
+    short_rows = inputs.banded_random(20_011, 200, 1, 8, seed=6)
+    for a in (long_rows, short_rows):
+        a = inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind, a.val.astype(np.float64))
+        x = xvec(a, dtype)
+        for h in (1, 8, 32):
+            check_spmv(b, convert(b, a, h, False, dtype), a, x, 0, dtype)
+
+
 def test_spmv_degenerate(b):
     # nnz = 0 with rows > 0: y = 0
     a = inputs.from_lengths(np.zeros(100, int), 10, seed=1)
