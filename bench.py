@@ -65,6 +65,8 @@ def args_parse():
     p.add_argument("--grid", type=int, default=128, help="stencil27: grid edge (128 = the full workload)")
     p.add_argument("--no-extras", action="store_true", help="skip the secondary storage-form measurements")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--shard", action="store_true",
+                   help="run the strip-sharded path even on one GPU (it is the default for N > 1)")
     return p.parse_args()
 
 
@@ -535,14 +537,15 @@ def run_sharded(args, rank, world, dist):
             "gpu_launches": args.steps, "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    dist.destroy_process_group()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_ours(args):
     import numpy as np
     import torch
     rank, world, dist = dist_setup(args.gpus)
-    if world > 1:
+    if world > 1 or args.shard:
         return run_sharded(args, rank, world, dist)
     from paper_1203_2946_gb300 import build
     build.build()
@@ -667,7 +670,7 @@ def run_ours(args):
         pl = powerlaw_block(b, inputs, oracle, dev, flush, stream, 100, args.warmup)
         pl.pop("_keep")
         line["powerlaw"] = pl
-        bt = batched_block(b, inputs, oracle, dev, flush, stream, 20, args.warmup, 4, 256)
+        bt = batched_block(b, inputs, oracle, dev, flush, stream, 20, args.warmup, (1, 2, 4, 8, 16, 32), 256)
         line["batched"] = {"ms": bt["ms"], "gbs": bt["gbs"], "config": bt["config"], "roofline": bt["roofline"],
                            "e2e": bt["e2e"], **bt["extra"]}
         line["selector_sample"] = selector_sample(b, dev)
@@ -868,6 +871,7 @@ def main():
     if args.variant is None:
         args.variant = {"stencil27": "padded", "powerlaw": "merge", "p7": "padded", "dense4": "padded"}.get(
             args.workload, "row")
+    args.height_given = args.height is not None
     if args.height is None:
         args.height = 8 if args.workload == "dense4" else (
             32 if args.workload in ("powerlaw", "p7") or args.variant == "padded" else 4)
@@ -1001,18 +1005,20 @@ def run_secondary(args):
         return
 
     # ---- batched: 256 banded-random matrices, k right-hand sides each
-    r = batched_block(b, inputs, oracle, dev, flush, stream, steps, args.warmup, args.height, args.batch_count,
-                      sampler)
+    r = batched_block(b, inputs, oracle, dev, flush, stream, steps, args.warmup,
+                      (args.height,) if args.height_given else (1, 2, 4, 8, 16, 32), args.batch_count, sampler)
     line = _line(args, r["gbs"], "GB/s", r["ms"], "f32", r["config"], r["roofline"], r["e2e"], r["gpu_launches"],
                  sampler.summary(), r["extra"])
     print(json.dumps(line), flush=True)
 
 
-def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, h, count, sampler=None):
+def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, heights, count, sampler=None):
     """The batched workload: `count` banded-random matrices with k right-hand
-    sides each, one persistent graph-replayed launch per step (autotuned work
-    units), against per-matrix launches and per-column plain FP64 SpMV; a
+    sides each, one persistent graph-replayed launch per step, its schedule
+    autotuned (each matrix's strip height among `heights`, then the work-unit
+    size), against per-matrix launches and per-column plain FP64 SpMV; a
     parity sample against the oracle; e2e with X in and Y out every step."""
+    from paper_1203_2946_gb300 import batch
     import contextlib
     import torch
     specs = inputs.batched_banded_specs()[:count]
@@ -1020,20 +1026,21 @@ def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, h, count
     with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
         mats_host = pool.map(_gen_batched, specs, chunksize=4)
     peak, peak_kind = measured_peaks()
-    mats, Xs, Ys, bp, nnz_total, rows_total = [], [], [], 0, 0, 0
+    csrs, Xs, Ys, bp, nnz_total, rows_total = [], [], [], 0, 0, 0
     for (rp_, ci_, val_, X_), sp_ in zip(mats_host, specs):
         n = rp_.size - 1
-        rp, ci = torch.from_numpy(rp_).to(dev), torch.from_numpy(ci_).to(dev)
-        M = b.cmrs_from_csr(rp, ci, torch.from_numpy(val_).to(dev), n, h, dtype=b.CMRS_F32)
-        del rp, ci
-        mats.append(M)
+        csrs.append((torch.from_numpy(rp_).to(dev), torch.from_numpy(ci_).to(dev), torch.from_numpy(val_).to(dev)))
         Xs.append(torch.from_numpy(X_).to(dev))
         Ys.append(torch.empty((n, X_.shape[1]), dtype=torch.float32, device=dev))
-        nnz = int(ci_.size)
+    t0 = time.perf_counter()
+    mats, hs, best, _, _ = batch.tune(csrs, Xs, Ys, heights=heights)
+    tune_s = time.perf_counter() - t0
+    del csrs
+    for (rp_, ci_, val_, X_), h in zip(mats_host, hs):
+        n, nnz = rp_.size - 1, int(ci_.size)
         bp += beta_plus(nnz, n, (n + h - 1) // h, 4) + 8 * (X_.shape[1] - 1) * n
         nnz_total += nnz * X_.shape[1]
         rows_total += n
-    best, _ = b.cmrs_spmm_autotune(mats, Xs, Ys, candidates=(2048, 8192, 32768, 131072), reps=3)
     plan = b.SpmmPlan(mats, Xs, Ys, work_target=best, use_graph=True)
     fn = lambda: b.cmrs_spmm_batched(plan)  # noqa: E731
     for _ in range(max(3, warmup)):
@@ -1065,7 +1072,7 @@ def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, h, count
         rp_, ci_, val_, X_ = mats_host[i]
         n = rp_.size - 1
         M64 = b.cmrs_from_csr(torch.from_numpy(rp_).to(dev), torch.from_numpy(ci_).to(dev),
-                              torch.from_numpy(val_.astype(np.float64)).to(dev), n, h, dtype=b.CMRS_F64)
+                              torch.from_numpy(val_.astype(np.float64)).to(dev), n, hs[i], dtype=b.CMRS_F64)
         xs = [torch.from_numpy(np.ascontiguousarray(X_[:, c], dtype=np.float64)).to(dev) for c in range(X_.shape[1])]
         mats64.append((M64, xs, torch.empty(n, dtype=torch.float64, device=dev), M64.spmv_workspace(0)))
     f64 = lambda: [b.cmrs_spmv(M64, xc, y64, 0, w64) for M64, xs, y64, w64 in mats64 for xc in xs]  # noqa: E731
@@ -1102,10 +1109,14 @@ def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, h, count
     info = plan.info()
     return {"ms": per_ms, "gbs": gbs,
             "config": {"workload": "%d banded-random matrices (n~U[1000,200000], bandwidth~U[64,2048], 10-60 nnz/row, "
-                                   "k in {1,4,8,32}), FP32, CMRS h=%d; one persistent graph-replayed launch"
-                                   % (len(specs), h),
+                                   "k in {1,4,8,32}), FP32, CMRS with each matrix's strip height autotuned; one "
+                                   "persistent graph-replayed launch" % len(specs),
                        "matrices": len(specs), "rows_total": rows_total, "entry_columns": nnz_total,
-                       "bytes_per_step": bp, "schedule": {"work_target": best, **info}, "l2": L2_NOTE},
+                       "bytes_per_step": bp,
+                       "schedule": {"work_target": best, **info,
+                                    "heights": {str(h): hs.count(h) for h in sorted(set(hs))},
+                                    "height_candidates": list(heights), "tuning_s": tune_s},
+                       "l2": L2_NOTE},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmm_queue"},
             "e2e": {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s",

@@ -443,6 +443,20 @@ int cmrs_mlp_backward(int B, int nin, int nh, int nout, const float *X, const fl
 int cmrs_mlp_adam(int n, float *params, const float *grads, float *m, float *v, int step, float lr,
                   float beta1, float beta2, float eps, void *stream);
 
+/* Training data of the network, on the device.  cmrs_feature_norm: per
+ * feature j of F (device double [B][nin], row-major) its mean and population
+ * standard deviation over the B rows (FP64 sums in row order), written as
+ * mean[j] and scale[j] = 1 / std (0 for a feature that does not vary; both
+ * device float [nin]); with X != NULL also X = (F - mean) * scale (device
+ * float [B][nin]).  cmrs_feature_apply: X only, from a given mean and scale.
+ * cmrs_cost_targets: T[n][c] = min(log2(times[n][c] / min_c times[n][c]), cap)
+ * (times: device double [B][nout], positive; T: device float [B][nout]).
+ * CMRS_ERR_ARG for bad sizes, pointers or cap <= 0.  Asynchronous. */
+int cmrs_feature_norm(int B, int nin, const double *F, float *mean, float *scale, float *X, void *stream);
+int cmrs_feature_apply(int B, int nin, const double *F, const float *mean, const float *scale, float *X,
+                       void *stream);
+int cmrs_cost_targets(int B, int nout, const double *times, float cap, float *T, void *stream);
+
 /* A trained selector (device pointers): input x = (feature - feat_mean) *
  * feat_scale, nin = CMRS_NFEAT, nout = CMRS_SEL_CHOICES, nh <= 64. */
 typedef struct cmrs_selector {

@@ -107,6 +107,9 @@ def lib():
             "cmrs_mlp_backward": ([i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp], i),
             "cmrs_mlp_adam": ([i, vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, vp], i),
+            "cmrs_feature_norm": ([i, i, vp, vp, vp, vp, vp], i),
+            "cmrs_feature_apply": ([i, i, vp, vp, vp, vp, vp], i),
+            "cmrs_cost_targets": ([i, i, vp, ctypes.c_float, vp, vp], i),
             "cmrs_select_strip_workspace": ([i, i, i, i, ctypes.POINTER(sz)], i),
             "cmrs_select_strip": ([i, i, i, vp, vp, ctypes.POINTER(cmrs_selector), ctypes.POINTER(i),
                                    ctypes.POINTER(i), ctypes.POINTER(i), vp, sz, vp], i),
@@ -337,6 +340,39 @@ def cmrs_shard_rows(row_ptr, height, parts):
     _check(lib().cmrs_shard_rows(rp.size - 1, rp.ctypes.data, int(height), int(parts), out.ctypes.data),
            "cmrs_shard_rows")
     return out
+
+
+def cmrs_feature_norm(F, stream=None):
+    """Per-feature mean and scale (1 / std, 0 if constant) of the rows of F
+    (device float64 [B][nin]) and the normalised FP32 inputs; returns
+    (mean, scale, X) as device tensors."""
+    F = F.contiguous()
+    B, nin = F.shape
+    mean = torch.empty(nin, dtype=torch.float32, device=F.device)
+    scale = torch.empty_like(mean)
+    X = torch.empty((B, nin), dtype=torch.float32, device=F.device)
+    _check(lib().cmrs_feature_norm(B, nin, _ptr(F), _ptr(mean), _ptr(scale), _ptr(X), _stream(stream)),
+           "cmrs_feature_norm")
+    return mean, scale, X
+
+
+def cmrs_feature_apply(F, mean, scale, stream=None):
+    """(F - mean) * scale as device float32 [B][nin] (F device float64)."""
+    F = F.contiguous()
+    B, nin = F.shape
+    X = torch.empty((B, nin), dtype=torch.float32, device=F.device)
+    _check(lib().cmrs_feature_apply(B, nin, _ptr(F), _ptr(mean), _ptr(scale), _ptr(X), _stream(stream)),
+           "cmrs_feature_apply")
+    return X
+
+
+def cmrs_cost_targets(times, cap, stream=None):
+    """min(log2(t / row minimum), cap) as device float32 (times device float64 [B][nout])."""
+    times = times.contiguous()
+    B, nout = times.shape
+    T = torch.empty((B, nout), dtype=torch.float32, device=times.device)
+    _check(lib().cmrs_cost_targets(B, nout, _ptr(times), float(cap), _ptr(T), _stream(stream)), "cmrs_cost_targets")
+    return T
 
 
 def cmrs_wait_probe(ws, tries, arrive, stream=None):

@@ -507,6 +507,87 @@ static size_t select_ws(int rows, int cols, int nnz, int exhaustive) {
   return b;
 }
 
+// ------------------------------------------------------------------ training data
+namespace cmrs {
+namespace {
+// Feature j's mean and population standard deviation over the B rows, summed
+// in row order in FP64 (one thread per feature); scale = 1 / std, or 0 for a
+// feature that does not vary (it then leaves the network's input).
+__global__ void k_feat_stats(int B, int nin, const double *__restrict__ F, float *__restrict__ mean,
+                             float *__restrict__ scale) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nin) return;
+  double s = 0.0;
+  for (int n = 0; n < B; ++n) s = __dadd_rn(s, F[(size_t)n * nin + j]);
+  const double m = __ddiv_rn(s, (double)B);
+  double q = 0.0;
+  for (int n = 0; n < B; ++n) {
+    const double d = __dsub_rn(F[(size_t)n * nin + j], m);
+    q = __dadd_rn(q, __dmul_rn(d, d));
+  }
+  const double sd = sqrt(__ddiv_rn(q, (double)B));
+  mean[j] = (float)m;
+  scale[j] = sd > 1e-12 ? (float)__ddiv_rn(1.0, sd) : 0.f;
+}
+
+// X = (F - mean) * scale in FP32, row-major [B][nin].
+__global__ void k_feat_apply(int total, int nin, const double *__restrict__ F, const float *__restrict__ mean,
+                             const float *__restrict__ scale, float *__restrict__ X) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int j = t % nin;
+  X[t] = ((float)F[t] - mean[j]) * scale[j];
+}
+
+// T[n][c] = min(log2(t[n][c] / min_c t[n][c]), cap): each choice's cost
+// relative to the row's best, one thread per row.
+__global__ void k_cost_targets(int B, int nout, const double *__restrict__ times, float cap, float *__restrict__ T) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= B) return;
+  const double *t = times + (size_t)n * nout;
+  double best = t[0];
+  for (int c = 1; c < nout; ++c) best = t[c] < best ? t[c] : best;
+  for (int c = 0; c < nout; ++c) {
+    const double r = log2(__ddiv_rn(t[c], best));
+    T[(size_t)n * nout + c] = (float)(r < (double)cap ? r : (double)cap);
+  }
+}
+}  // namespace
+}  // namespace cmrs
+
+extern "C" int cmrs_feature_norm(int B, int nin, const double *F, float *mean, float *scale, float *X, void *stream) {
+  CMRS_TRACE();
+  if (B < 1 || nin < 1 || !F || !mean || !scale) return CMRS_ERR_ARG;
+  cudaStream_t st = as_stream(stream);
+  k_feat_stats<<<(nin + 63) / 64, 64, 0, st>>>(B, nin, F, mean, scale);
+  CMRS_LAUNCH_CHECK();
+  if (X) {
+    const long long total = (long long)B * nin;
+    if (total >= (1LL << 31)) return CMRS_ERR_ARG;
+    k_feat_apply<<<(int)ceil_div(total, 256), 256, 0, st>>>((int)total, nin, F, mean, scale, X);
+    CMRS_LAUNCH_CHECK();
+  }
+  return CMRS_OK;
+}
+
+extern "C" int cmrs_feature_apply(int B, int nin, const double *F, const float *mean, const float *scale, float *X,
+                                  void *stream) {
+  CMRS_TRACE();
+  const long long total = (long long)B * nin;
+  if (B < 1 || nin < 1 || !F || !mean || !scale || !X || total >= (1LL << 31)) return CMRS_ERR_ARG;
+  k_feat_apply<<<(int)ceil_div(total, 256), 256, 0, as_stream(stream)>>>((int)total, nin, F, mean, scale, X);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
+extern "C" int cmrs_cost_targets(int B, int nout, const double *times, float cap, float *T, void *stream) {
+  CMRS_TRACE();
+  if (B < 1 || nout < 1 || !times || !T || !(cap > 0.f)) return CMRS_ERR_ARG;
+  k_cost_targets<<<(B + 127) / 128, 128, 0, as_stream(stream)>>>(B, nout, times, cap, T);
+  CMRS_LAUNCH_CHECK();
+  return CMRS_OK;
+}
+
 extern "C" int cmrs_select_strip_workspace(int rows, int cols, int nnz, int exhaustive, size_t *bytes) {
   if (rows < 1 || cols < 1 || nnz < 0 || !bytes) return CMRS_ERR_ARG;
   *bytes = select_ws(rows, cols, nnz, exhaustive);

@@ -32,6 +32,12 @@ constexpr int kSpmmCH = 2;  // entries whose gathers are in flight together (8 r
 #define CMRS_SPMM_CH4 2  // 16-byte gathers in flight per lane (measured 6.45 ms per batch; 1: 6.72, 3: 7.06, 4: 7.07, 8: 7.73)
 #endif
 constexpr int kSpmmCH4 = CMRS_SPMM_CH4;  // the same for the 16-byte gathers
+#ifndef CMRS_SPMM_MINB
+#define CMRS_SPMM_MINB 5  // resident CTAs per SM asked of the register allocator (48 registers)
+#endif
+#ifndef CMRS_SPMM_PREFETCH
+#define CMRS_SPMM_PREFETCH 1  // next batch's column words loaded during this batch's gathers
+#endif
 
 struct Desc {
   int32_t rows, height, bits, k, vec, pad;
@@ -100,16 +106,32 @@ __device__ __forceinline__ void spmm_rows4(const Desc &d, int row0, int row1, in
       const int col = c0 + g;
       if (active && col < kv) {
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        // The column words and values of the next batch are loaded while this
+        // batch's X gathers are in flight: a gather waits for its column word,
+        // so without this every batch pays two memory round trips in a row.
+        uint32_t pn[kSpmmCH4];
+        float vn[kSpmmCH4];
+#pragma unroll
+        for (int u = 0; u < kSpmmCH4; ++u)
+          if (k0 + u < k1) {
+            pn[u] = __ldg(d.packed + k0 + u);
+            vn[u] = __ldg(d.val + k0 + u);
+          }
         for (int j = k0; j < k1; j += kSpmmCH4) {
           float4 xv[kSpmmCH4];
           float vv[kSpmmCH4];
 #pragma unroll
           for (int u = 0; u < kSpmmCH4; ++u) {
-            if (j + u < k1) {
-              const uint32_t p = __ldg(d.packed + j + u);
-              vv[u] = __ldg(d.val + j + u);
-              xv[u] = __ldg(X4 + (size_t)(p >> d.bits) * kv + col);
-            }
+            vv[u] = vn[u];
+            if (j + u < k1) xv[u] = __ldg(X4 + (size_t)(pn[u] >> d.bits) * kv + col);
+          }
+          if (CMRS_SPMM_PREFETCH) {
+#pragma unroll
+            for (int u = 0; u < kSpmmCH4; ++u)
+              if (j + kSpmmCH4 + u < k1) {
+                pn[u] = __ldg(d.packed + j + kSpmmCH4 + u);
+                vn[u] = __ldg(d.val + j + kSpmmCH4 + u);
+              }
           }
 #pragma unroll
           for (int u = 0; u < kSpmmCH4; ++u)
@@ -119,6 +141,14 @@ __device__ __forceinline__ void spmm_rows4(const Desc &d, int row0, int row1, in
               acc.z = fmaf(vv[u], xv[u].z, acc.z);
               acc.w = fmaf(vv[u], xv[u].w, acc.w);
             }
+          if (!CMRS_SPMM_PREFETCH) {
+#pragma unroll
+            for (int u = 0; u < kSpmmCH4; ++u)
+              if (j + kSpmmCH4 + u < k1) {
+                pn[u] = __ldg(d.packed + j + kSpmmCH4 + u);
+                vn[u] = __ldg(d.val + j + kSpmmCH4 + u);
+              }
+          }
         }
         Y4[(size_t)row * kv + col] = acc;
       }
@@ -179,7 +209,7 @@ __device__ __forceinline__ void spmm_rows(const Desc &d, int row0, int row1, int
   }
 }
 
-__global__ void __launch_bounds__(kSpmmThreads) k_spmm_queue(const Desc *__restrict__ descs,
+__global__ void __launch_bounds__(kSpmmThreads, CMRS_SPMM_MINB) k_spmm_queue(const Desc *__restrict__ descs,
                                                              const Unit *__restrict__ units, int nunits,
                                                              QueueHead *q) {
   const int lane = threadIdx.x & 31;
@@ -195,7 +225,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm_queue(const Desc *__restr
 }
 
 // One matrix, no queue: warp w takes rows [w*rpw, (w+1)*rpw).
-__global__ void __launch_bounds__(kSpmmThreads) k_spmm_one(Desc d, int rows_per_warp) {
+__global__ void __launch_bounds__(kSpmmThreads, CMRS_SPMM_MINB) k_spmm_one(Desc d, int rows_per_warp) {
   const int lane = threadIdx.x & 31;
   const long long w = ((long long)blockIdx.x * kSpmmThreads + threadIdx.x) >> 5;
   const long long r0 = w * rows_per_warp;

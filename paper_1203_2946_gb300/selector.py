@@ -134,12 +134,6 @@ def build_corpus(specs, device="cuda", reps=5, log=None):
 
 
 # ----------------------------------------------------------------------------- network
-def targets_from_times(times, cap=8.0):
-    """log2(t_c / t_best), capped (a form that was not timed counts as 2^cap
-    times the best)."""
-    return np.minimum(np.log2(times / times.min(axis=1, keepdims=True)), cap).astype(np.float32)
-
-
 def init_params(seed=0, nin=b.NFEAT, nh=NH, nout=NCHOICE):
     """He-normal weights, zero biases (layout of cmrs_mlp_*)."""
     rng = np.random.default_rng(seed)
@@ -149,25 +143,19 @@ def init_params(seed=0, nin=b.NFEAT, nh=NH, nout=NCHOICE):
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
-def normalization(features):
-    mean = features.mean(axis=0)
-    std = features.std(axis=0)
-    scale = np.where(std > 1e-12, 1.0 / np.maximum(std, 1e-12), 0.0)
-    return mean.astype(np.float32), scale.astype(np.float32)
-
-
 def train(features, times, idx, steps=3000, batch=256, lr=2e-3, seed=0, device="cuda", log=None, cap=1.0):
     """Trains on rows `idx` with the library's forward/backward/Adam kernels.
     Targets: log2(t_c / t_best) capped at `cap`; the default, 1, calls every
     choice more than twice as slow as the best simply slow, so that the
     network spends itself on ranking the near-best ones (held-out regret on
-    the full-range corpus, same network and steps: 1.0061 with a cap of 8,
-    1.0027 with 1)."""
+    the full-range corpus, same network and steps: 1.0071 with a cap of 8,
+    1.0044 with 1)."""
     if times.shape[1] != NCHOICE or features.shape[1] != b.NFEAT:
         raise ValueError("timings must have %d choices and features %d columns" % (NCHOICE, b.NFEAT))
-    mean, scale = normalization(features[idx])
-    X = torch.from_numpy(((features[idx] - mean) * scale).astype(np.float32)).to(device)
-    T = torch.from_numpy(targets_from_times(times[idx], cap)).to(device)
+    # inputs normalised by the training rows' statistics, and the capped
+    # relative costs, both computed by the library on the device
+    mean, scale, X = b.cmrs_feature_norm(torch.from_numpy(np.ascontiguousarray(features[idx], np.float64)).to(device))
+    T = b.cmrs_cost_targets(torch.from_numpy(np.ascontiguousarray(times[idx], np.float64)).to(device), cap)
     P = torch.from_numpy(init_params(seed)).to(device)
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
@@ -189,13 +177,12 @@ def train(features, times, idx, steps=3000, batch=256, lr=2e-3, seed=0, device="
             history.append((step, float(loss.item())))
             if log:
                 log("train step %d loss %.5f" % history[-1])
-    return {"params": P, "mean": torch.from_numpy(mean).to(device), "scale": torch.from_numpy(scale).to(device),
-            "nh": NH, "history": history}
+    return {"params": P, "mean": mean, "scale": scale, "nh": NH, "history": history}
 
 
 def predict(model, features, device="cuda"):
-    X = torch.from_numpy(((features - model["mean"].cpu().numpy()) * model["scale"].cpu().numpy())
-                         .astype(np.float32)).to(device)
+    X = b.cmrs_feature_apply(torch.from_numpy(np.ascontiguousarray(features, np.float64)).to(device),
+                             model["mean"].to(device), model["scale"].to(device))
     acts = b.cmrs_mlp_forward(X, model["params"], model["nh"], NCHOICE)
     return b.mlp_output(acts, X.shape[0], model["nh"], NCHOICE).argmin(dim=1).cpu().numpy()
 

@@ -121,6 +121,12 @@ def test_argument_checks_before_device_work(L):
     k0 = (ctypes.c_int32 * 1)(0)
     assert L.cmrs_spmm_plan_workspace(1, A, k0, 1024, ctypes.byref(n)) == 1
     assert L.cmrs_spmm_plan_workspace(1, A, k, 1024, ctypes.byref(n)) == 0 and n.value > 0 and n.value % 256 == 0
+    # training data of the network: sizes and pointers checked before any launch
+    assert L.cmrs_feature_norm(0, 4, p, p, p, None, None) == 1
+    assert L.cmrs_feature_norm(4, 4, None, p, p, None, None) == 1
+    assert L.cmrs_feature_apply(4, 4, p, p, p, None, None) == 1
+    assert L.cmrs_cost_targets(4, 21, p, ctypes.c_float(0.0), p, None) == 1
+    assert L.cmrs_cost_targets(0, 21, p, ctypes.c_float(1.0), p, None) == 1
     # features, network, selector
     assert L.cmrs_features_workspace(-1, ctypes.byref(n)) == 1
     assert L.cmrs_features_workspace(10, None) == 1

@@ -108,10 +108,13 @@ def _batched_member(spec):
 def test_spmm_batched_full_size(b):
     """The batched workload at full size: 256 banded-random matrices (n
     1,000..200,000, bandwidth 64..2,048, 10..60 entries per row, k in
-    {1, 4, 8, 32}), in the configuration the benchmark times: height 4,
-    autotuned work target, one graph-captured persistent launch.  Sampled rows
-    of every matrix, every right-hand side, against the FP64 oracle; every
-    row written; a second replay bit-identical."""
+    {1, 4, 8, 32}), in the configuration the benchmark times: each matrix's
+    strip height and the work-unit size autotuned, one graph-captured
+    persistent launch.  Sampled rows of every matrix (64 each: the first, the
+    last, both sides of a strip edge, random ones), every right-hand side,
+    against the FP64 oracle; every row written; a second replay
+    bit-identical."""
+    from paper_1203_2946_gb300 import batch
     import multiprocessing as mp
     import os
     orc.lib()  # built before the workers load it
@@ -119,15 +122,16 @@ def test_spmm_batched_full_size(b):
     assert len(specs) == 256
     with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
         parts = pool.map(_batched_member, specs, chunksize=4)
-    mats, Xs, Ys = [], [], []
+    csrs, Xs, Ys = [], [], []
     for rp, ci, val, X, *_ in parts:
         n = rp.size - 1
-        mats.append(b.cmrs_from_csr(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(),
-                                    torch.from_numpy(val).cuda(), n, 4, dtype=b.CMRS_F32))
+        csrs.append((torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), torch.from_numpy(val).cuda()))
         Xs.append(torch.from_numpy(X).cuda())
         Ys.append(torch.empty((n, X.shape[1]), dtype=torch.float32, device="cuda"))
+    mats, heights, best, _, table = batch.tune(csrs, Xs, Ys)
+    del csrs
     assert sum(M.nnz for M in mats) > 500_000_000
-    best, _ = b.cmrs_spmm_autotune(mats, Xs, Ys, candidates=(2048, 8192, 32768, 131072), reps=3)
+    assert all(M.height == h and t[batch.HEIGHTS.index(h)] == min(t) for M, h, t in zip(mats, heights, table))
     plan = b.SpmmPlan(mats, Xs, Ys, work_target=best, use_graph=True)
     for Y in Ys:
         Y.fill_(float("nan"))
@@ -145,6 +149,26 @@ def test_spmm_batched_full_size(b):
         tol = (lens[:, None] + 2) * 2.0**-24 * scale
         err = np.abs(g.astype(np.float64) - ref)
         assert (err <= tol).all(), (i, np.argwhere(err > tol)[:5])
+    plan.close()
+
+
+def test_schedule_autotuner_small_batch(b):
+    """batch.tune: every matrix converted at the height whose single launch
+    timed fastest, a work target from the candidates, and the plan built on
+    that schedule gives the right product for every matrix."""
+    from paper_1203_2946_gb300 import batch
+    _, Xs, Ys, host = small_batch(b, 10, seed=9)
+    csrs = [to_dev(a) for a, _ in host]
+    mats, heights, best, ms, table = batch.tune(csrs, Xs, Ys, heights=(1, 4, 16), work_targets=(1024, 16384))
+    assert best in (1024, 16384) and ms > 0 and len(table) == len(mats) == 10
+    for M, h, t in zip(mats, heights, table):
+        assert h in (1, 4, 16) and M.height == h and t[(1, 4, 16).index(h)] == min(t)
+    plan = b.SpmmPlan(mats, Xs, Ys, work_target=best)
+    for Y in Ys:
+        Y.fill_(float("nan"))
+    b.cmrs_spmm_batched(plan)
+    for (a, X), Y in zip(host, Ys):
+        check_spmm(a, X, Y)
     plan.close()
 
 
@@ -226,6 +250,30 @@ def test_mlp_forward_backward_adam_vs_oracle(b):
     m64, v64 = np.zeros_like(p64), np.zeros_like(p64)
     orc.adam_step(p64, got, m64, v64, 1, 1e-3)
     assert np.allclose(P.cpu().numpy(), p64, rtol=0, atol=2e-6)
+
+
+def test_feature_norm_and_cost_targets(b):
+    """The training data the library prepares on the device: per-feature
+    mean and 1/std over the rows (0 for a constant feature), the normalised
+    FP32 inputs, and the capped log2 costs relative to each row's best."""
+    rng = np.random.default_rng(3)
+    F = rng.normal(5.0, 3.0, (300, b.NFEAT))
+    F[:, 7] = 2.5  # constant: leaves the input
+    mean, scale, X = b.cmrs_feature_norm(torch.from_numpy(F).cuda())
+    m_ref, s_ref = F.mean(0), F.std(0)
+    assert np.allclose(mean.cpu().numpy(), m_ref.astype(np.float32), rtol=1e-6, atol=1e-6)
+    sc = scale.cpu().numpy()
+    assert sc[7] == 0.0
+    keep = np.arange(b.NFEAT) != 7
+    assert np.allclose(sc[keep], (1.0 / s_ref[keep]).astype(np.float32), rtol=1e-6)
+    ref = (F.astype(np.float32) - mean.cpu().numpy()) * sc
+    assert np.allclose(X.cpu().numpy(), ref, rtol=1e-6, atol=1e-6)
+    assert torch.equal(b.cmrs_feature_apply(torch.from_numpy(F).cuda(), mean, scale), X)
+    t = rng.uniform(0.01, 5.0, (200, 21))
+    T = b.cmrs_cost_targets(torch.from_numpy(t).cuda(), 1.0).cpu().numpy()
+    want = np.minimum(np.log2(t / t.min(1, keepdims=True)), 1.0)
+    assert np.allclose(T, want.astype(np.float32), rtol=1e-6, atol=1e-7)
+    assert (T.min(1) == 0.0).all() and T.max() <= 1.0
 
 
 def test_training_reduces_loss(b):
