@@ -346,10 +346,10 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU leg
-def kernel_section_sha1(begin, end):
-    """sha1 of the source text of one kernel section of spmv.cu (from the line
-    holding `begin` up to the line holding `end`)."""
-    src = open(os.path.join(ROOT, "paper_1203_2946_gb300", "csrc", "spmv.cu")).read()
+def kernel_section_sha1(begin, end, source="spmv.cu"):
+    """sha1 of the source text of one kernel section of a csrc file (from the
+    line holding `begin` up to the line holding `end`)."""
+    src = open(os.path.join(ROOT, "paper_1203_2946_gb300", "csrc", source)).read()
     a = src.index(begin)
     b = src.index(end, a + len(begin))
     return hashlib.sha1(src[a:b].encode()).hexdigest()
@@ -362,7 +362,7 @@ def traffic_record(kernel, workload):
     try:
         with open(path) as f:
             rec = json.load(f)[kernel][workload]
-        h = kernel_section_sha1(*rec["section"])
+        h = kernel_section_sha1(*rec["section"], source=rec.get("source_file", "spmv.cu"))
         return rec["bytes_per_launch"] if rec.get("section_sha1") == h else None
     except Exception:
         return None
@@ -1012,6 +1012,18 @@ def run_secondary(args):
     print(json.dumps(line), flush=True)
 
 
+def spmm_traffic(bp):
+    """DRAM bytes per batch: the ncu capture of the first 16 matrices scaled by
+    their algorithmic bytes to the whole batch (its traffic equals its
+    algorithmic bytes to 1%), while the kernel's source is unchanged."""
+    t = traffic_record("k_spmm_queue", "batched16")
+    if t is None:
+        return None
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        alg = json.load(f)["k_spmm_queue"]["batched16"]["algorithmic_bytes"]
+    return int(t / alg * bp)
+
+
 def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, heights, count, sampler=None):
     """The batched workload: `count` banded-random matrices with k right-hand
     sides each, one persistent graph-replayed launch per step, its schedule
@@ -1118,7 +1130,8 @@ def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, heights,
                                     "height_candidates": list(heights), "tuning_s": tune_s},
                        "l2": L2_NOTE},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "peak_kind": peak_kind + " (hbm_gbs)", "traffic": None, "kernel": "k_spmm_queue"},
+                         "peak_kind": peak_kind + " (hbm_gbs)", "traffic": spmm_traffic(bp),
+                         "kernel": "k_spmm_queue"},
             "e2e": {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s",
                     "h2d_bytes_per_step": int(Xh.numel() * 4), "d2h_bytes_per_step": int(Yh[0].numel() * 4),
                     "ms_per_step": e_ms, "note": "X in and Y out in one copy each per step (every matrix's block "
