@@ -33,7 +33,10 @@ constexpr int kRowCap = 32 * CMRS_ROW_ROWS;   // ROW: entries per shared-memory 
 #ifndef CMRS_MERGE_MINB_F32
 #define CMRS_MERGE_MINB_F32 5
 #endif
-constexpr int kMergeThreads = 128;
+#ifndef CMRS_MERGE_THREADS
+#define CMRS_MERGE_THREADS 128  // threads per MERGE tile (a CTA)
+#endif
+constexpr int kMergeThreads = CMRS_MERGE_THREADS;
 #ifndef CMRS_MERGE_E
 #define CMRS_MERGE_E 15
 #endif
