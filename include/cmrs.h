@@ -39,7 +39,7 @@ extern "C" {
 #define CMRS_ERR_COL_OVERFLOW 3 /* cols > 2^(32 - bits): column does not fit the packed word */
 #define CMRS_ERR_CSR_INVALID 4  /* RowPtr not a valid CRS row pointer, or a column outside [0, cols) */
 #define CMRS_ERR_CUDA 5         /* a CUDA runtime call failed; cmrs_last_cuda_error() has the code */
-#define CMRS_ERR_UNSUPPORTED 6  /* valid request this build does not implement (e.g. variant on sorted strips) */
+#define CMRS_ERR_UNSUPPORTED 6  /* valid request this library does not implement (e.g. variant on sorted strips) */
 #define CMRS_ERR_WORKSPACE 7    /* workspace pointer null/misaligned or smaller than its query returned */
 #define CMRS_ERR_TIMEOUT 8      /* a bounded in-kernel wait gave up; the output is not valid */
 

@@ -231,7 +231,7 @@ void orc_cmrs_spmv(int rows, int height, const int32_t *strip_ptr,
 
 /* ------------------------------------------------------------------------ */
 /* Value storage forms.  The paper stores Val as float or double (Section
- * 6.2).  The reduced forms below are this build's own definitions, written
+ * 6.2).  The reduced forms below are this library's own definitions, written
  * with integer operations so that the stored bits are unambiguous:
  *   F32   : (float)v, IEEE round to nearest even.
  *   BF16  : the upper 16 bits of the FP32 pattern of (float)v, rounded to
