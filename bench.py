@@ -661,6 +661,11 @@ def run_ours(args):
         line["variants_f64"] = variant_sweep(b, a, xd, M_csr, flush, stream, bp)
         line["modified_cmrs"] = modified_cmrs(b, a, xd, rp, ci, va, flush, stream)
         line["heights_f64_row"] = height_sweep(b, a, xd, rp, ci, va, flush, stream)
+        plain = line["heights_f64_row"]["h4"]["ms"]
+        line["speedup_vs_plain_f64_cmrs"] = {
+            "plain": "plain CMRS h=4 (the paper's best single FP64 height on its K20M, Section 6.2), FP64, ROW", "plain_ms": plain,
+            "speedup": plain / per_ms,
+            "by_form": {k: plain / v["ms"] for k, v in line["forms"].items()}}
         line["strip_sorted_vs_unsorted_f64"] = sorted_strips(b, a, xd, rp, ci, va, flush, stream)
         line["selector"] = selector_cost(b, a, rp, ci)
         line["conversion"] = conversion_times(b, a, rp, ci, va, M_csr, h,
