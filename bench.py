@@ -500,15 +500,20 @@ def run_sharded(args, rank, world, dist):
     bp = beta_plus(a.nnz, a.rows, (a.rows + h - 1) // h, 8)
     for _ in range(max(3, args.warmup)):
         S.step()
-    sampler = ClockSampler(None)
+    pci = getattr(torch.cuda.get_device_properties(dev), "pci_bus_id", None)
+    sampler = ClockSampler(pci)
     barrier(dist)
     torch.cuda.synchronize()
+    # every rank must run the same number of steps (each holds collectives):
+    # a warm-up counted in steps, not in seconds
+    warm = max(16, args.warmup)
     with sampler:
-        times = time_steps(S.step, args.steps, flush, stream, warm_steps=max(3, args.warmup), warm_s=0.25)
+        times = time_steps(S.step, args.steps, flush, stream, warm_steps=warm, warm_s=0.0)
     barrier(dist)
     total_ms = max_over_ranks(dist, sum(times))
     per_ms = total_ms / args.steps
-    local_ms = max_over_ranks(dist, statistics.mean(time_steps(S.product, 20, flush, stream)))
+    local_ms = max_over_ranks(dist, statistics.mean(time_steps(S.product, 20, flush, stream, warm_steps=warm,
+                                                               warm_s=0.0)))
     # e2e: this rank's piece of x in from pinned host memory, exchange, product, its rows of y out
     xh = torch.from_numpy(np.ascontiguousarray(x[S.r0:S.r1])).pin_memory()
     yh = torch.empty(S.rows, dtype=torch.float64).pin_memory()
@@ -517,7 +522,8 @@ def run_sharded(args, rank, world, dist):
         S.x_local().copy_(xh, non_blocking=True)
         S.step()
         yh.copy_(S.y, non_blocking=True)
-    e_ms = max_over_ranks(dist, statistics.mean(time_steps(e2e_step, 20, lambda i: None, stream)))
+    e_ms = max_over_ranks(dist, statistics.mean(time_steps(e2e_step, 20, lambda i: None, stream, warm_steps=warm,
+                                                           warm_s=0.0)))
     gbs = bp / (per_ms / 1e3) / 1e9
     line = {"metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "strong",
