@@ -490,7 +490,12 @@ def run_sharded(args, rank, world, dist):
     from paper_1203_2946_gb300 import binding as b, inputs, shard
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    a, x = inputs.workload_stencil27_128()
+    g = args.grid
+    if g == 128:
+        a, x = inputs.workload_stencil27_128()
+    else:
+        a = inputs.stencil_3d_27pt(g, g, g, seed=1)
+        x = inputs.uniform_vector(a.cols, 0)
     h = args.height
     slots = args.slots if args.variant == "padded" else None
     S = shard.ShardedSpmv(a, rank, world, h, dtype=b.CMRS_F64, slots=slots, device=dev)
@@ -524,12 +529,22 @@ def run_sharded(args, rank, world, dist):
         yh.copy_(S.y, non_blocking=True)
     e_ms = max_over_ranks(dist, statistics.mean(time_steps(e2e_step, 20, lambda i: None, stream, warm_steps=warm,
                                                            warm_s=0.0)))
+    # this rank's rows against the FP64 oracle (its rows of A times the whole x)
+    import oracle
+    S.step()
+    from paper_1203_2946_gb300.shard import local_rows
+    lrp, lci, lva = local_rows(a.row_ptr, a.col_ind, a.val, S.r0, S.r1)
+    err = 0.0
+    if S.rows > 0:
+        yref, scale = oracle.csr_spmv(lrp, lci, lva, x)
+        err = float(np.max(np.abs(S.y.cpu().numpy() - yref) / np.where(scale > 0, scale, 1)))
+    err = max_over_ranks(dist, err)
     gbs = bp / (per_ms / 1e3) / 1e9
     line = {"metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "27-point stencil 128^3 (n=%d, nnz=%d), FP64, %s, split over %d GPUs by strips"
-                                   % (a.rows, a.nnz, ("modified CMRS h=%d, M=%d" % (h, slots)) if slots else
+            "config": {"workload": "27-point stencil %d^3 (n=%d, nnz=%d), FP64, %s, split over %d GPUs by strips"
+                                   % (g, a.rows, a.nnz, ("modified CMRS h=%d, M=%d" % (h, slots)) if slots else
                                       "CMRS h=%d" % h, world),
                        "height": h, "slots": slots, "bytes_per_step": bp, "row_bounds": [int(v) for v in S.bounds],
                        "l2": L2_NOTE, "parallelism": "strip shards x%d, x exchanged by NCCL broadcasts" % world},
@@ -537,6 +552,7 @@ def run_sharded(args, rank, world, dist):
                          "frac": gbs / world / peak, "peak_kind": peak_kind + " (hbm_gbs), per GPU",
                          "traffic": None, "kernel": "k_spmv_padded" if slots else "k_spmv_row"},
             "local_product_ms_max_over_ranks": local_ms,
+            "err_vs_f64_oracle_max_over_ranks": err,
             "e2e": {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
                     "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(yh.numel() * 8),
                     "note": "per rank: its piece of x in, exchange, product, its rows of y out (max over ranks)"},

@@ -54,3 +54,22 @@ def test_sharded_product_more_parts_than_strips(b):
     y = sharded_product(b, a, x, 8, 16, b.CMRS_F64)  # 3 strips, 8 parts: 5 ranks hold no rows
     yref, scale = orc.csr_spmv(a.row_ptr, a.col_ind, a.val, x)
     assert np.all(np.abs(y - yref) <= 1e-12 * scale)
+
+
+def test_bench_sharded_path_runs_and_checks(b):
+    """bench.py's strip-sharded path (the one torchrun runs for N > 1), on one
+    GPU with --shard: a JSON line with its row bounds, strong scaling, and
+    the rank's product equal to the oracle's."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--shard", "--grid", "40", "--steps", "3",
+                          "--warmup", "3", "--no-cpu"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["scaling"] == "strong" and line["n_gpus"] == 1
+    assert line["config"]["row_bounds"] == [0, 40 ** 3]
+    assert line["value"] > 0 and line["e2e"]["value"] > 0
+    assert line["err_vs_f64_oracle_max_over_ranks"] <= 1e-12
