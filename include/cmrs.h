@@ -76,17 +76,17 @@ extern "C" {
 /* ---- SpMV kernel variants -------------------------------------------------
  * Every variant computes the same y = A x; they differ in how threads are
  * mapped onto strips (Section 4 gives one warp per strip).
- *   CMRS_VARIANT_ROW    heights dividing 32 and at most 28 entries per row
- *                       on average: a lane per row -- a warp bulk-copies the
- *                       entries of 32 consecutive rows (whole strips) into
- *                       its own shared-memory stage and lane r sums row r in
- *                       a register (a range longer than the stage, sized
- *                       from the mean row length, is read from global
- *                       memory).  Otherwise: a few threads per row (4 for
- *                       CMRS_F64, 2 for the other forms), each summing a
- *                       contiguous share, a CTA staging the strips of 128
- *                       consecutive rows.  Needs unsorted strips.  Best for
- *                       regular rows.
+ *   CMRS_VARIANT_ROW    mean rows of at most 28, 56 or 112 entries and a
+ *                       height dividing 32, 16 or 8: L = 1, 2 or 4 lanes per
+ *                       row -- a warp bulk-copies the entries of 32 / L
+ *                       consecutive rows (whole strips) into its own
+ *                       shared-memory stage and the row's L lanes sum it in
+ *                       registers (a range longer than the stage, sized from
+ *                       the mean row length, is read from global memory).
+ *                       Otherwise: a few threads per row (4 for CMRS_F64, 2
+ *                       for the other forms), each summing a contiguous
+ *                       share, a CTA staging the strips of 128 consecutive
+ *                       rows.  Needs unsorted strips.  Best for regular rows.
  *   CMRS_VARIANT_STRIP  Algorithm 1 of Section 4: one warp per strip, lanes
  *                       stride through the strip and accumulate per-row
  *                       partial sums in a shared-memory buffer buf[row][lane],

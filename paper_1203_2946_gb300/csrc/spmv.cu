@@ -391,6 +391,9 @@ __global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int
 #ifndef CMRS_LANE_MAX_MU
 #define CMRS_LANE_MAX_MU 28.0  // mean entries per row up to which ROW takes the lane mapping
 #endif
+#ifndef CMRS_LANE_MAX_L
+#define CMRS_LANE_MAX_L 4  // most lanes sharing a row (1, 2 or 4)
+#endif
 #ifndef CMRS_LANE_WARPS
 #define CMRS_LANE_WARPS 4
 #endif
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(RowCfg<DT>::kThreads) k_spmv_row(int rows, int
 constexpr int kLaneCap = CMRS_LANE_CAP;
 constexpr int kLaneWarps = CMRS_LANE_WARPS;
 
-template <int DT>
+template <int DT, int L>
 __global__ void __launch_bounds__(kLaneWarps * 32) k_spmv_lane(int rows, int height, int bits, int cap, int nnz,
                                                               const int32_t *__restrict__ sp,
                                                               const uint32_t *__restrict__ packed,
@@ -429,18 +432,20 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_spmv_lane(int rows, int hei
   __syncwarp();
   uint64_t pol = 0;
   if (lane == 0) pol = policy_evict_first();
-  const long long units = ((long long)rows + 31) / 32;
+  constexpr int R = 32 / L;  // rows per unit: L lanes share a row
+  const int q = lane & (L - 1), slot = lane / L;
+  const long long units = ((long long)rows + R - 1) / R;
   const long long nw = (long long)gridDim.x * kLaneWarps;
   uint32_t phase = 0;
   for (long long u = (long long)blockIdx.x * kLaneWarps + w; u < units; u += nw) {
-    const long long r0 = u * 32;
-    const long long r1 = min(r0 + 32, (long long)rows);
+    const long long r0 = u * R;
+    const long long r1 = min(r0 + R, (long long)rows);
     const int s0 = (int)(r0 / height), s1 = (int)((r1 - 1) / height) + 1;  // the unit's strips
     const int ea = sp[s0], eb = sp[s1];
     const bool staged = eb - ea <= cap;  // warp-uniform
     if (staged && lane == 0) issue_stage<DT>(ea, eb, nnz, packed, hi, lo, stg, cap, &bars[w], pol, &info[w]);
     // this lane's row and its strip's bounds, loaded while the copy is in flight
-    const long long row = r0 + lane;
+    const long long row = r0 + slot;
     const bool active = row < rows;
     const int s = active ? (int)(row / height) : s0;
     const uint32_t rr = active ? (uint32_t)(row - (long long)s * height) : 0;
@@ -460,14 +465,21 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_spmv_lane(int rows, int hei
                          : (Stage<DT>::kSplit ? lo : hi);
     const long long base = staged ? info[w].a8 : 0;
     // row r ends where row r + 1 starts, or at its strip's end (the height
-    // divides 32, so lane 31's row is the last of its strip)
+    // divides R, so the unit's last row is the last of its strip); the row's
+    // first lane searches, its L lanes share the result
     int k0 = sa;
-    if (active && rr > 0) k0 = lb_ris(cp, base, sa, sb, rr, mask);
-    const int nxt = __shfl_down_sync(kAll, k0, 1);
-    int k1 = (rr + 1 == (uint32_t)height || row + 1 >= rows || lane == 31) ? sb : nxt;
+    if (active && rr > 0 && q == 0) k0 = lb_ris(cp, base, sa, sb, rr, mask);
+    if (L > 1) k0 = __shfl_sync(kAll, k0, lane & ~(L - 1));
+    const int nxt = __shfl_down_sync(kAll, k0, L);
+    int k1 = (rr + 1 == (uint32_t)height || row + 1 >= rows || slot == R - 1) ? sb : nxt;
     if (!active) k0 = k1 = 0;
-    const A acc = seg_dot<DT, CH, 1>(cp, vh, vl, base, k0, k1, bits, x);
-    if (active) {
+    // lane q of the row's L takes the q-th contiguous share of it
+    const int seg = (k1 - k0 + L - 1) / L;
+    const int a0 = min(k1, k0 + q * seg), a1 = min(k1, a0 + seg);
+    A acc = seg_dot<DT, CH, 1>(cp, vh, vl, base, a0, a1, bits, x);
+#pragma unroll
+    for (int o = L / 2; o >= 1; o >>= 1) acc += __shfl_down_sync(kAll, acc, o);
+    if (active && q == 0) {
       const long long t = row_map ? row_map[row] : row;  // y position (row map of a reordered matrix)
       if (t >= 0 && t < rows) y[t] = acc;
     }
@@ -1394,21 +1406,35 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
   Acc *y = reinterpret_cast<Acc *>(yv);
   uint32_t *status = reinterpret_cast<uint32_t *>(ws);
   const int sms = sm_count();
-  if (variant == CMRS_VARIANT_ROW && CMRS_ROW_LANE && 32 % A->height == 0 &&
-      (double)A->nnz <= CMRS_LANE_MAX_MU * A->rows) {
-    // stage: 1.25x the entries of an average 32 rows, in multiples of 32, at
-    // most kLaneCap -- short rows leave shared memory for more warps; a
-    // longer unit is read from global memory
-    static Occ occ[kLaneCap / 32 + 1];
-    const double mu = A->rows > 0 ? (double)A->nnz / A->rows : 0.0;
-    const int cap = (int)std::min<long long>(kLaneCap, std::max<long long>(128, ceil_div((long long)(CMRS_LANE_SLACK * mu), 32) * 32));
+  const double mu = A->rows > 0 ? (double)A->nnz / A->rows : 0.0;
+  const int lanes = mu <= CMRS_LANE_MAX_MU                              ? 1
+                    : (CMRS_LANE_MAX_L >= 2 && mu <= 2 * CMRS_LANE_MAX_MU) ? 2
+                    : (CMRS_LANE_MAX_L >= 4 && mu <= 4 * CMRS_LANE_MAX_MU) ? 4
+                                                                          : 0;
+  if (variant == CMRS_VARIANT_ROW && CMRS_ROW_LANE && lanes && (32 / lanes) % A->height == 0) {
+    // stage: 1.25x the entries of an average unit (32 / lanes rows), in
+    // multiples of 32, at most kLaneCap -- short rows leave shared memory for
+    // more warps; a longer unit is read from global memory
+    const int cap = (int)std::min<long long>(
+        kLaneCap, std::max<long long>(128, ceil_div((long long)(CMRS_LANE_SLACK * mu / lanes), 32) * 32));
     const size_t smem = (size_t)kLaneWarps * Stage<DT>::bytes(cap);
-    const int per_sm = occupancy(k_spmv_lane<DT>, kLaneWarps * 32, smem, occ[cap / 32],
-                                 (size_t)kLaneWarps * Stage<DT>::bytes(kLaneCap));
-    const long long need = ceil_div(ceil_div(A->rows, 32), kLaneWarps);
+    const size_t smem_max = (size_t)kLaneWarps * Stage<DT>::bytes(kLaneCap);
+    const long long need = ceil_div(ceil_div(A->rows, 32 / lanes), kLaneWarps);
+    static Occ occ1[kLaneCap / 32 + 1], occ2[kLaneCap / 32 + 1], occ4[kLaneCap / 32 + 1];
+    int per_sm = 1;
+    if (lanes == 1) per_sm = occupancy(k_spmv_lane<DT, 1>, kLaneWarps * 32, smem, occ1[cap / 32], smem_max);
+    if (lanes == 2) per_sm = occupancy(k_spmv_lane<DT, 2>, kLaneWarps * 32, smem, occ2[cap / 32], smem_max);
+    if (lanes == 4) per_sm = occupancy(k_spmv_lane<DT, 4>, kLaneWarps * 32, smem, occ4[cap / 32], smem_max);
     const int grid = (int)std::min<long long>(need, (long long)per_sm * sms);
-    k_spmv_lane<DT><<<grid, kLaneWarps * 32, smem, st>>>(A->rows, A->height, A->bits, cap, A->nnz, A->strip_ptr,
-                                                          A->col_packed, hi, lo, x, y, row_map, status);
+    if (lanes == 1)
+      k_spmv_lane<DT, 1><<<grid, kLaneWarps * 32, smem, st>>>(A->rows, A->height, A->bits, cap, A->nnz,
+                                                               A->strip_ptr, A->col_packed, hi, lo, x, y, row_map, status);
+    else if (lanes == 2)
+      k_spmv_lane<DT, 2><<<grid, kLaneWarps * 32, smem, st>>>(A->rows, A->height, A->bits, cap, A->nnz,
+                                                               A->strip_ptr, A->col_packed, hi, lo, x, y, row_map, status);
+    else
+      k_spmv_lane<DT, 4><<<grid, kLaneWarps * 32, smem, st>>>(A->rows, A->height, A->bits, cap, A->nnz,
+                                                               A->strip_ptr, A->col_packed, hi, lo, x, y, row_map, status);
     CMRS_LAUNCH_CHECK();
   } else if (variant == CMRS_VARIANT_ROW) {
     static Occ occ;

@@ -214,12 +214,15 @@ def test_spmv_skewed_rows(b, dtype):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_spmv_row_lane_long_units(b, dtype):
-    """ROW at heights dividing 32 gives a lane per row: 32 rows of 40..60
-    entries pass through the warp's stage in chunks, and rows of 1..8 entries
-    (with a tail that is not a multiple of 32) in one copy each."""
+    """ROW on plain CMRS with one, two or four lanes per row (mean rows up to
+    28, 56, 112 entries; heights dividing the unit of 32, 16, 8 rows), each
+    unit staged in the warp's shared memory: rows of 1..8, 40..60 and
+    70..100 entries, tails that are not a multiple of the unit, and h = 32
+    where the wider units fall back to the share-per-thread kernel."""
     long_rows = inputs.banded_random(20_003, 900, 40, 60, seed=5)
+    longer_rows = inputs.banded_random(9_001, 1200, 70, 100, seed=7)
     short_rows = inputs.banded_random(20_011, 200, 1, 8, seed=6)
-    for a in (long_rows, short_rows):
+    for a in (long_rows, longer_rows, short_rows):
         a = inputs.CSR(a.rows, a.cols, a.row_ptr, a.col_ind, a.val.astype(np.float64))
         x = xvec(a, dtype)
         for h in (1, 8, 32):
