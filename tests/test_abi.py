@@ -146,8 +146,10 @@ def test_argument_checks_before_device_work(L):
 
 def test_auto_variant_rule(L):
     """CMRS_VARIANT_AUTO: STRIP on sorted strips; otherwise MERGE for mean row
-    length < 2 or > 32 or a strip above 8 x height x mean (or unknown), ROW
-    for the rest.  Host only: the device pointers are never read."""
+    length < 2, or > 32 where ROW's two- or four-lanes-per-row mapping does
+    not apply (mean up to 56 at heights dividing 16, 112 at heights dividing
+    8), or a strip above 8 x height x mean (or unknown); ROW for the rest.
+    Host only: the device pointers are never read."""
     from paper_1203_2946_gb300 import binding as b
 
     def resolve(rows, nnz, height, max_strip, flags=0, variant=-1):
@@ -165,7 +167,13 @@ def test_auto_variant_rule(L):
     assert resolve(1000, 2000, 4, 8) == (0, ROW)               # mean exactly 2
     assert resolve(1000, 1999, 4, 8) == (0, MERGE)             # mean below 2
     assert resolve(1000, 32000, 4, 128) == (0, ROW)            # mean exactly 32
-    assert resolve(1000, 32001, 4, 129) == (0, MERGE)          # mean above 32
+    assert resolve(1000, 32001, 32, 1025) == (0, MERGE)        # mean above 32, no lanes mapping at h = 32
+    assert resolve(1000, 32001, 16, 513) == (0, ROW)           # two lanes per row (h divides 16)
+    assert resolve(1000, 56000, 16, 896) == (0, ROW)           # mean exactly 56
+    assert resolve(1000, 56001, 16, 897) == (0, MERGE)         # mean above 56, h does not divide 8
+    assert resolve(1000, 56001, 4, 225) == (0, ROW)            # four lanes per row (h divides 8)
+    assert resolve(1000, 112000, 8, 896) == (0, ROW)           # mean exactly 112
+    assert resolve(1000, 112001, 8, 897) == (0, MERGE)         # mean above 112
     assert resolve(1000, 10000, 4, 320) == (0, ROW)            # strip exactly 8 x 4 x 10
     assert resolve(1000, 10000, 4, 321) == (0, MERGE)          # skewed strip
     assert resolve(1000, 10000, 4, -1) == (0, MERGE)           # unknown longest strip
