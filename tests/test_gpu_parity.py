@@ -383,7 +383,7 @@ def test_paper_extra_matrices(b, which):
     check_spmv(b, P, a, x, b.CMRS_VARIANT_PADDED, 0)
 
 
-@pytest.mark.parametrize("case", ["stencil", "short", "long", "skewed", "sorted"])
+@pytest.mark.parametrize("case", ["stencil", "short", "long", "very_long", "skewed", "sorted"])
 def test_auto_variant(b, case):
     """CMRS_VARIANT_AUTO runs the variant cmrs_spmv_variant names: its y is
     bit-identical to that variant's and passes the oracle bar."""
@@ -392,8 +392,10 @@ def test_auto_variant(b, case):
         a, want = inputs.stencil_3d_27pt(20, 20, 20, seed=3), b.CMRS_VARIANT_ROW
     elif case == "short":
         a, want = inputs.from_lengths(rng.integers(0, 3, 30000), 30000, seed=4), b.CMRS_VARIANT_MERGE
-    elif case == "long":
-        a, want = inputs.from_lengths(np.full(300, 100), 5000, seed=5), b.CMRS_VARIANT_MERGE
+    elif case == "long":  # four lanes per row at h = 4
+        a, want = inputs.from_lengths(np.full(300, 100), 5000, seed=5), b.CMRS_VARIANT_ROW
+    elif case == "very_long":
+        a, want = inputs.from_lengths(np.full(300, 150), 5000, seed=5), b.CMRS_VARIANT_MERGE
     elif case == "skewed":
         L = rng.integers(4, 9, 20000)
         L[100] = 5000
