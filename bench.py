@@ -1350,6 +1350,8 @@ def run_irregular(args):
             ("reordered_w4096_padded_m1", b.cmrs_pad(M4096, 1), b.CMRS_VARIANT_PADDED, p4096),
             ("reordered_w4096_padded_m2", b.cmrs_pad(M4096, 2), b.CMRS_VARIANT_PADDED, p4096),
             ("row_h32", M0, b.CMRS_VARIANT_ROW, None),
+            ("row_h16_two_lanes_per_row", b.cmrs_from_csr(rp, ci, va, a.cols, 16, dtype=b.CMRS_F64), b.CMRS_VARIANT_ROW,
+             None),
             ("merge_h32", M0, b.CMRS_VARIANT_MERGE, None),
             ("reordered_w4096_row_h32", M4096, b.CMRS_VARIANT_ROW, p4096)):
         w2 = mat.spmv_workspace(v)
