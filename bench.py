@@ -550,7 +550,7 @@ def run_sharded(args, rank, world, dist):
                        "l2": L2_NOTE, "parallelism": "strip shards x%d, x exchanged by NCCL broadcasts" % world},
             "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": peak, "unit": "GB/s",
                          "frac": gbs / world / peak, "peak_kind": peak_kind + " (hbm_gbs), per GPU",
-                         "traffic": None, "kernel": "k_spmv_padded" if slots else "k_spmv_row"},
+                         "traffic": None, "kernel": "k_spmv_padded" if slots else row_kernel(S.M)},
             "local_product_ms_max_over_ranks": local_ms,
             "err_vs_f64_oracle_max_over_ranks": err,
             "e2e": {"value": bp / (e_ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": e_ms,
@@ -636,7 +636,7 @@ def run_ours(args):
     e2e_ms = max_over_ranks(dist, e2e_pipelined(lambda xv, yv: b.cmrs_spmv(M, xv, yv, binding_variant, ws), xh, xds,
                                                 yds, yhs, e2e_steps))
 
-    kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[variant]
+    kname = {0: row_kernel(M), 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[variant]
     split = variant == 3 and ws.numel() > 256  # a padded workspace past the status word: strips split over warps
     if split:
         kname = "k_spmv_padded_split"  # + k_pad_combine
@@ -1013,7 +1013,7 @@ def run_secondary(args):
         yhs = [torch.empty(a.rows, dtype=xd.dtype).pin_memory() for _ in range(2)]
         e_ms = e2e_pipelined(lambda xv, yv: b.cmrs_spmv(M, xv, yv, v, ws), xh, [xd, torch.empty_like(xd)],
                              [yd, torch.empty_like(yd)], yhs, max(20, min(steps, 200)))
-        kname = {0: "k_spmv_row", 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[ran]
+        kname = {0: row_kernel(M), 1: "k_spmv_strip", 2: "k_spmv_merge", 3: "k_spmv_padded"}[ran]
         split = ran == 3 and ws.numel() > 256  # a padded workspace past the status word: strips split over warps
         if split:
             kname = "k_spmv_padded_split"  # + k_pad_combine
@@ -1170,6 +1170,17 @@ def batched_block(b, inputs, oracle, dev, flush, stream, steps, warmup, heights,
                                                     "batched_f32_ms_same_subset": plain_sub_ms,
                                                     "speedup_of_f32_spmm": f64_sub_ms / plain_sub_ms},
                       "parity_sample": {"matrices": 8, "max_err_over_tolerance": worst}}}
+
+
+def row_kernel(M):
+    """The kernel the library's ROW variant runs for matrix M: one, two or
+    four lanes per row (k_spmv_lane) for mean rows of at most 28, 56, 112
+    entries at heights dividing 32, 16, 8; else k_spmv_row."""
+    mu = M.nnz / max(M.rows, 1)
+    for lanes, bound in ((1, 28), (2, 56), (4, 112)):
+        if mu <= bound:
+            return "k_spmv_lane" if (32 // lanes) % M.height == 0 else "k_spmv_row"
+    return "k_spmv_row"
 
 
 def gather_floor(b, ci, va, x32, flush, stream, kernel_ms, steps=50):
