@@ -298,8 +298,9 @@ int cmrs_spmv_rows(const cmrs_matrix *A, const void *x, void *y, const int32_t *
  * with CMRS_VARIANT_MERGE, same arguments without the workspace, but takes
  * its scratch from one fixed 2 MiB array compiled into the library (a
  * file-scope __device__ array, resident on every GPU that loads the library
- * until the process exits).  Limit: A->nnz <= 111,820,800 (58,240 tiles of
- * 1,920 entries); larger matrices return CMRS_ERR_WORKSPACE before any device
+ * until the process exits).  Limit: 58,240 MERGE tiles, i.e. A->nnz <=
+ * 67,092,480 for CMRS_F64 (tiles of 1,152 entries) and <= 82,001,920 for the
+ * other forms (1,408 entries); larger matrices return CMRS_ERR_WORKSPACE before any device
  * work.  Unsorted, unpadded strips only (CMRS_ERR_UNSUPPORTED otherwise).  No
  * cudaMalloc, cudaFree or other allocating call is made.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress, with

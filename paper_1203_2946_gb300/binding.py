@@ -138,6 +138,19 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
 
 
+def _operand(t, dtype, n, name):
+    """The C ABI takes bare device pointers and reads or writes n elements of
+    the matrix's value type there: check the tensor before its pointer goes."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s is %s; this matrix's value form takes %s" % (name, t.dtype, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() < n:
+        raise ValueError("%s holds %d elements; the product needs %d" % (name, t.numel(), n))
+
+
 def _check(rc, where):
     if rc != CMRS_OK:
         raise CmrsError(rc, where)
@@ -272,8 +285,11 @@ def cmrs_permute_csr(row_ptr, col_ind, val, perm, stream=None):
 
 def cmrs_spmv_rows(A: Matrix, x, row_map, y=None, variant=CMRS_VARIANT_AUTO, workspace_tensor=None, stream=None):
     """y[row_map[i]] = (A x)_i: the product of a row-reordered matrix in the original order."""
+    _operand(x, A.x_dtype, A.cols, "x")
     if y is None:
         y = torch.empty(A.rows, dtype=A.x_dtype, device=x.device)
+    _operand(y, A.x_dtype, A.rows, "y")
+    _operand(row_map, torch.int32, A.rows, "row_map")
     v = variant
     ws = workspace_tensor if workspace_tensor is not None else A.spmv_workspace(
         CMRS_VARIANT_ROW if v == CMRS_VARIANT_AUTO and cmrs_spmv_variant(A, v) == CMRS_VARIANT_MERGE else v)
@@ -285,8 +301,10 @@ def cmrs_spmv_rows(A: Matrix, x, row_map, y=None, variant=CMRS_VARIANT_AUTO, wor
 
 def cmrs_spmv(A: Matrix, x, y=None, variant=CMRS_VARIANT_AUTO, workspace_tensor=None, stream=None):
     """y = A x on the device; y is allocated if not given and returned."""
+    _operand(x, A.x_dtype, A.cols, "x")
     if y is None:
         y = torch.empty(A.rows, dtype=A.x_dtype, device=x.device)
+    _operand(y, A.x_dtype, A.rows, "y")
     ws = workspace_tensor if workspace_tensor is not None else A.spmv_workspace(variant)
     rc = lib().cmrs_spmv(A.ref(), _ptr(x), _ptr(y), variant, _ptr(ws), ws.numel(), _stream(stream))
     _check(rc, "cmrs_spmv")
@@ -303,8 +321,10 @@ def cmrs_spmv_variant(A: Matrix, variant=CMRS_VARIANT_AUTO):
 def cmrs_spmv_noalloc(A: Matrix, x, y=None, stream=None):
     """y = A x with no workspace and no device allocation by the library (the
     library's fixed scratch array; see cmrs.h for its limit and sharing)."""
+    _operand(x, A.x_dtype, A.cols, "x")
     if y is None:
         y = torch.empty(A.rows, dtype=A.x_dtype, device=x.device)
+    _operand(y, A.x_dtype, A.rows, "y")
     _check(lib().cmrs_spmv_noalloc(A.ref(), _ptr(x), _ptr(y), _stream(stream)), "cmrs_spmv_noalloc")
     return y
 
@@ -411,14 +431,21 @@ def stored_values(A: Matrix):
 def cmrs_spmm(A: Matrix, X, Y=None, stream=None):
     """Y = A X for one CMRS_F32 matrix; X [cols][k] row-major float32."""
     k = X.shape[1]
+    _operand(X, torch.float32, A.cols * k, "X")
     if Y is None:
         Y = torch.empty((A.rows, k), dtype=torch.float32, device=X.device)
+    _operand(Y, torch.float32, A.rows * k, "Y")
     _check(lib().cmrs_spmm(A.ref(), k, _ptr(X), _ptr(Y), _stream(stream)), "cmrs_spmm")
     return Y
 
 
 def _batch_arrays(mats, Xs, Ys):
     n = len(mats)
+    if not (len(Xs) == n and len(Ys) == n):
+        raise ValueError("one X and one Y per matrix")
+    for M, X, Y in zip(mats, Xs, Ys):
+        _operand(X, torch.float32, M.cols * X.shape[1], "X")
+        _operand(Y, torch.float32, M.rows * X.shape[1], "Y")
     A = (ctypes.POINTER(cmrs_matrix) * n)(*[ctypes.pointer(m.struct) for m in mats])
     k = (ctypes.c_int32 * n)(*[int(X.shape[1]) for X in Xs])
     Xp = (ctypes.c_void_p * n)(*[X.data_ptr() for X in Xs])

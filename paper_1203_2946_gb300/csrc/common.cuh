@@ -42,6 +42,8 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 int sm_count();  // multiprocessors of the current device (cached per device)
+// bytes of workspace the MERGE mapping needs for nnz entries of value form dtype
+size_t merge_workspace_bytes(int nnz, int dtype);
 
 // Programmatic dependent launch: `kernel` may begin while the kernel before
 // it in the stream is still running, once every block of that kernel has

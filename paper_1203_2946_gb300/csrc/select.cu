@@ -502,7 +502,7 @@ static size_t select_ws(int rows, int cols, int nnz, int exhaustive) {
     // padded forms: StripPtr, items (packed + FP32 values) and the layout pass's workspace
     b += align256(((size_t)rows / 16 + 2) * 4) + 2 * align256(pad_cap(rows, nnz) * 4) + align256(256) +
          align256(((size_t)rows / 16 + 2) * 4) + align256(((size_t)rows / 16 + 2) * 8) + align256(((size_t)rows / 16 / 1024 + 2) * 8);
-    b += align256(256 + ((size_t)nnz / 1920 + 2) * 40 + 4096);
+    b += align256(merge_workspace_bytes(nnz, CMRS_F32) + 4096);
   }
   return b;
 }

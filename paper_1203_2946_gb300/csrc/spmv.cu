@@ -24,29 +24,55 @@ namespace {
 #endif
 constexpr int kRowThreads = CMRS_ROW_ROWS;    // ROW: rows per block
 constexpr int kRowCap = 32 * CMRS_ROW_ROWS;   // ROW: entries per shared-memory stage
-// Resident CTAs per SM asked of the register allocator (shared memory allows
-// about 5): FP64 at 4 keeps 128 registers, the FP32-accumulated forms at 5
-// keep 96, both without spills.
+// MERGE per value form (FP64; the FP32-accumulated forms): entries per
+// thread (odd, so that a warp's shared loads hit 32 banks), resident CTAs
+// per SM asked of the register allocator, and the CTAs per SM the launch
+// keeps (its shared-memory carveout holds that many and no more, the rest of
+// the SM's L1/shared storage stays L1).  The x gathers miss L1 and each miss
+// in flight holds an L1 line: with two stages of 15 entries a thread at 5
+// CTAs, the FP32 tiles left 92 KB of L1 and FP64 (4 CTAs) 60 KB, and a
+// further 8 KB of shared memory per CTA, leaving 28 KB, took the power-law
+// FP32 product from 143 to 222 us.  FP32: 11 entries at 6 CTAs (80
+// registers); FP64: 9 at 5 CTAs (96 registers); both keep 92 KB of L1.
+#ifndef CMRS_MERGE_E_F64
+#define CMRS_MERGE_E_F64 9
+#endif
+#ifndef CMRS_MERGE_E_F32
+#define CMRS_MERGE_E_F32 11
+#endif
 #ifndef CMRS_MERGE_MINB_F64
-#define CMRS_MERGE_MINB_F64 4
+#define CMRS_MERGE_MINB_F64 5
 #endif
 #ifndef CMRS_MERGE_MINB_F32
-#define CMRS_MERGE_MINB_F32 5
+#define CMRS_MERGE_MINB_F32 6
 #endif
 #ifndef CMRS_MERGE_THREADS
 #define CMRS_MERGE_THREADS 128  // threads per MERGE tile (a CTA)
 #endif
 constexpr int kMergeThreads = CMRS_MERGE_THREADS;
-#ifndef CMRS_MERGE_E
-#define CMRS_MERGE_E 15
-#endif
 #ifndef CMRS_MERGE_VSMEM
 #define CMRS_MERGE_VSMEM 0
 #endif
-constexpr int kMergeE = CMRS_MERGE_E;  // MERGE: entries per thread; odd, so that a warp's shared loads hit 32 banks
 // MERGE: values read from the staged tile at their multiply-add instead of held in registers
 constexpr bool kMergeVSmem = CMRS_MERGE_VSMEM != 0;
-constexpr int kMergeTile = kMergeThreads * kMergeE;
+#ifndef CMRS_MERGE_CTAS_F64
+#define CMRS_MERGE_CTAS_F64 5
+#endif
+#ifndef CMRS_MERGE_CTAS_F32
+#define CMRS_MERGE_CTAS_F32 6
+#endif
+// ROW's lane mapping: most resident CTAs per SM (0: as many as fit)
+#ifndef CMRS_LANE_CTAS
+#define CMRS_LANE_CTAS 0
+#endif
+template <int DT>
+struct MergeCfg {
+  static constexpr int E = DT == CMRS_F64 ? CMRS_MERGE_E_F64 : CMRS_MERGE_E_F32;
+  static constexpr int Tile = kMergeThreads * E;  // entries per tile, a multiple of 8
+  static constexpr int MinBlocks = DT == CMRS_F64 ? CMRS_MERGE_MINB_F64 : CMRS_MERGE_MINB_F32;
+  static constexpr int Ctas = DT == CMRS_F64 ? CMRS_MERGE_CTAS_F64 : CMRS_MERGE_CTAS_F32;
+  static_assert(E % 2 == 1 && Tile % 8 == 0, "MERGE: odd entries per thread, 8-entry-aligned tiles");
+};
 constexpr int kMergeWarps = kMergeThreads / 32;
 constexpr int kStripWarps = 8;
 constexpr int kStages = 2;
@@ -709,8 +735,8 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
 }
 
 // ============================================================== MERGE mapping
-// Tile t = entries [1920 t, 1920 t + 1920), staged by bulk copies; thread i
-// owns the 15 consecutive entries from 1920 t + 15 i.  It finds their strip by
+// Tile t = entries [T t, T t + T), T = 128 E, staged by bulk copies; thread i
+// owns the E consecutive entries from T t + E i (E = 9 for FP64, 11 else).  It finds their strip by
 // a binary search of StripPtr between the strips holding the tile's first
 // and next tile's first entry (tile_strip[], one small pre-pass), then walks
 // the entries: a row's run is summed by one FMA chain; a run that starts and
@@ -719,17 +745,18 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
 // the following threads' head partials in order); a run cut by the tile's end
 // goes to a tile record that a fix-up kernel joins in tile order.  Rows with
 // no entries are written as 0 by the thread owning the entry before the gap.
-__global__ void k_tile_map(int strips, const int32_t *__restrict__ sp, int ntiles, int32_t *__restrict__ tile_strip) {
+__global__ void k_tile_map(int strips, const int32_t *__restrict__ sp, int tile, int ntiles,
+                           int32_t *__restrict__ tile_strip) {
   pdl_launch_dependents();  // the product may start staging its first tiles
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= strips) return;
   const long long a = sp[s], b = sp[s + 1];
   if (b <= a) return;
-  for (long long t = (a + kMergeTile - 1) / kMergeTile; t * kMergeTile < b && t < ntiles; ++t) tile_strip[t] = s;
+  for (long long t = (a + tile - 1) / tile; t * tile < b && t < ntiles; ++t) tile_strip[t] = s;
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MINB_F64 : CMRS_MERGE_MINB_F32)
+__global__ void __launch_bounds__(kMergeThreads, MergeCfg<DT>::MinBlocks)
     k_spmv_merge(int rows, int height, int bits, int strips, int nnz,
                                                               const int32_t *__restrict__ sp,
                                                               const uint32_t *__restrict__ packed,
@@ -741,6 +768,7 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
                                                               TileRec *__restrict__ recs, uint32_t *status) {
   typedef typename Form<DT>::Stored S;
   typedef typename Form<DT>::Acc A;
+  constexpr int kMergeE = MergeCfg<DT>::E, kMergeTile = MergeCfg<DT>::Tile;
   extern __shared__ __align__(128) char smem[];
   __shared__ uint64_t bars[kStages];
   __shared__ StageInfo info[kStages];
@@ -788,6 +816,9 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
     const long long tb = min(ta + kMergeTile, (long long)nnz);
     const long long k0 = ta + (long long)tid * kMergeE;
     const long long k1 = min(k0 + kMergeE, tb);
+    auto put = [&](uint32_t row, A val) {
+      if (row < (uint32_t)rows) y[row] = val;
+    };
     uint8_t flags = 0;
     A hv = A(0), tv = A(0);      // head partial (row continued from before), tail partial (row going on)
     uint32_t hrow = 0, trow = 0;
@@ -849,7 +880,7 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
       else operands_and_rows(std::false_type{});
       // rows before the first entry of the matrix are empty
       if (k0 == 0)
-        for (uint32_t g = 0; g < rw[0] && g < (uint32_t)rows; ++g) y[g] = A(0);
+        for (uint32_t g = 0; g < rw[0] && g < (uint32_t)rows; ++g) put(g, A(0));
       // The sums: one FMA chain per run of equal rows, no branch around the
       // FMAs (a finished run leaves by a predicated store or a select), and
       // the warp reconverged first, so that every FMA issues for the whole
@@ -867,7 +898,7 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
             const bool nw = rw[j] != rw[j - 1];
             const bool to_head = nw && first && cont_in;  // first run continues a row from before k0
             head_sum = to_head ? acc : head_sum;
-            if (nw && !to_head && rw[j - 1] < (uint32_t)rows) y[rw[j - 1]] = acc;
+            if (nw && !to_head) put(rw[j - 1], acc);
             first = first && !nw;
             acc = nw ? A(0) : acc;
             acc = fma_acc(val_of(j), xv[j], acc);
@@ -884,7 +915,7 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
 #pragma unroll
           for (int j = 1; j < kMergeE; ++j)
             if (decltype(full)::value || j < n)
-              for (uint32_t g = rw[j - 1] + 1; g < rw[j] && g < (uint32_t)rows; ++g) y[g] = A(0);
+              for (uint32_t g = rw[j - 1] + 1; g < rw[j] && g < (uint32_t)rows; ++g) put(g, A(0));
         }
       };
       if (n == kMergeE) sums_and_gaps(std::true_type{});
@@ -913,12 +944,12 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
           tv = acc;
           trow = run_row;
           flags |= F_TAIL;
-        } else if (run_row < (uint32_t)rows) {
-          y[run_row] = acc;
+        } else {
+          put(run_row, acc);
         }
       }
       if (!cont_out)
-        for (long long g = (long long)run_row + 1; g < next_row && g < rows; ++g) y[g] = A(0);
+        for (long long g = (long long)run_row + 1; g < next_row && g < rows; ++g) put((uint32_t)g, A(0));
     }
     // Rows crossing thread boundaries, joined by a segmented scan over the
     // tile's threads in thread order.  A thread whose single run continues on
@@ -978,8 +1009,8 @@ __global__ void __launch_bounds__(kMergeThreads, DT == CMRS_F64 ? CMRS_MERGE_MIN
           recs[t].head_row = (int)hrow;
           recs[t].head_sum = (double)res;
           recs[t].head_flag = 1;
-        } else if (hrow < (uint32_t)rows) {
-          y[hrow] = res;
+        } else {
+          put(hrow, res);
         }
       }
       if (tid == kMergeThreads - 1) {
@@ -1306,9 +1337,13 @@ struct Occ {
 
 // Resident CTAs per SM for `smem` bytes of dynamic shared memory, cached per
 // device.  The kernel is first opted in to max(smem, smem_cap) bytes, the most
-// any launch of it asks for.
+// any launch of it asks for.  With max_per_sm > 0 the kernel's shared-memory
+// carveout is set to the smallest that holds max_per_sm CTAs, and the rest of
+// the SM's 256 KB of L1/shared storage stays L1: a kernel whose time goes to
+// x gathers that miss L1 keeps more of them in flight with more L1 lines to
+// hold them than with more resident warps.
 template <typename K>
-int occupancy(K kernel, int threads, size_t smem, Occ &cache, size_t smem_cap = 0) {
+int occupancy(K kernel, int threads, size_t smem, Occ &cache, size_t smem_cap = 0, int max_per_sm = 0) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
@@ -1316,15 +1351,27 @@ int occupancy(K kernel, int threads, size_t smem, Occ &cache, size_t smem_cap = 
   if (cache.val[dev] == 0) {
     // opt in to the dynamic shared memory the launches use (static + dynamic may pass 48 KB)
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(smem, smem_cap));
+    if (max_per_sm > 0) {
+      cudaFuncAttributes fa;
+      int sm_smem = 0;
+      if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess &&
+          cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+          sm_smem > 0) {
+        const size_t need = (size_t)max_per_sm * (std::max(smem, smem_cap) + fa.sharedSizeBytes + 1024);
+        const int pct = (int)std::min<size_t>(100, (need * 100 + sm_smem - 1) / sm_smem);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+      }
+    }
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    if (max_per_sm > 0) n = std::min(n, max_per_sm);
     cache.val[dev] = n;
   }
   return cache.val[dev];
 }
 
-size_t merge_ws_bytes(int nnz) {
-  const long long ntiles = ceil_div(nnz, kMergeTile);
+size_t merge_ws_bytes(int nnz, int dtype) {
+  const long long ntiles = ceil_div(nnz, dtype == CMRS_F64 ? MergeCfg<CMRS_F64>::Tile : MergeCfg<CMRS_F32>::Tile);
   return 256 + align256((size_t)(ntiles + 1) * 4) + align256((size_t)ntiles * sizeof(TileRec));
 }
 
@@ -1422,9 +1469,9 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
     const long long need = ceil_div(ceil_div(A->rows, 32 / lanes), kLaneWarps);
     static Occ occ1[kLaneCap / 32 + 1], occ2[kLaneCap / 32 + 1], occ4[kLaneCap / 32 + 1];
     int per_sm = 1;
-    if (lanes == 1) per_sm = occupancy(k_spmv_lane<DT, 1>, kLaneWarps * 32, smem, occ1[cap / 32], smem_max);
-    if (lanes == 2) per_sm = occupancy(k_spmv_lane<DT, 2>, kLaneWarps * 32, smem, occ2[cap / 32], smem_max);
-    if (lanes == 4) per_sm = occupancy(k_spmv_lane<DT, 4>, kLaneWarps * 32, smem, occ4[cap / 32], smem_max);
+    if (lanes == 1) per_sm = occupancy(k_spmv_lane<DT, 1>, kLaneWarps * 32, smem, occ1[cap / 32], smem_max, CMRS_LANE_CTAS);
+    if (lanes == 2) per_sm = occupancy(k_spmv_lane<DT, 2>, kLaneWarps * 32, smem, occ2[cap / 32], smem_max, CMRS_LANE_CTAS);
+    if (lanes == 4) per_sm = occupancy(k_spmv_lane<DT, 4>, kLaneWarps * 32, smem, occ4[cap / 32], smem_max, CMRS_LANE_CTAS);
     const int grid = (int)std::min<long long>(need, (long long)per_sm * sms);
     if (lanes == 1)
       k_spmv_lane<DT, 1><<<grid, kLaneWarps * 32, smem, st>>>(A->rows, A->height, A->bits, cap, A->nnz,
@@ -1463,13 +1510,14 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
     }
   } else {
     static Occ occ;
+    constexpr int kMergeTile = MergeCfg<DT>::Tile;
     const int ntiles = (int)ceil_div(A->nnz, kMergeTile);
     int32_t *tile_strip = reinterpret_cast<int32_t *>(ws + 256);
     TileRec *recs = reinterpret_cast<TileRec *>(ws + 256 + align256((size_t)(ntiles + 1) * 4));
-    k_tile_map<<<(int)ceil_div(A->strips, 256), 256, 0, st>>>(A->strips, A->strip_ptr, ntiles, tile_strip);
+    k_tile_map<<<(int)ceil_div(A->strips, 256), 256, 0, st>>>(A->strips, A->strip_ptr, kMergeTile, ntiles, tile_strip);
     CMRS_LAUNCH_CHECK();
     const size_t smem = kStages * Stage<DT>::bytes(kMergeTile);
-    const int per_sm = occupancy(k_spmv_merge<DT>, kMergeThreads, smem, occ);
+    const int per_sm = occupancy(k_spmv_merge<DT>, kMergeThreads, smem, occ, 0, MergeCfg<DT>::Ctas);
     const int grid = (int)std::min<long long>(ntiles, (long long)per_sm * sms);
     int rc = launch_pdl(k_spmv_merge<DT>, (unsigned)grid, kMergeThreads, smem, st, A->rows, A->height, A->bits,
                         A->strips, A->nnz, A->strip_ptr, A->col_packed, hi, lo, x, y, tile_strip, ntiles, recs, status);
@@ -1546,6 +1594,8 @@ extern "C" int cmrs_spmv_variant(const cmrs_matrix *A, int variant, int *resolve
   return resolve_variant(A, variant, resolved);
 }
 
+size_t cmrs::merge_workspace_bytes(int nnz, int dtype) { return merge_ws_bytes(nnz, dtype); }
+
 extern "C" int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *bytes) {
   if (!bytes) return CMRS_ERR_ARG;
   int rc = check_matrix(A);
@@ -1553,7 +1603,7 @@ extern "C" int cmrs_spmv_workspace(const cmrs_matrix *A, int variant, size_t *by
   int v = 0;
   rc = resolve_variant(A, variant, &v);
   if (rc) return rc;
-  *bytes = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz)
+  *bytes = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz, A->dtype)
            : v == CMRS_VARIANT_PADDED ? pad_split_ws_bytes(A, pad_parts(A))
                                        : 256;
   return CMRS_OK;
@@ -1577,7 +1627,7 @@ int spmv_impl(const cmrs_matrix *A, const void *x, void *y, const int32_t *row_m
   }
   if (A->rows == 0) return CMRS_OK;
   if (!y || (A->nnz > 0 && !x)) return CMRS_ERR_ARG;
-  const size_t need = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz) : 256;
+  const size_t need = v == CMRS_VARIANT_MERGE ? merge_ws_bytes(A->nnz, A->dtype) : 256;
   if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CMRS_ERR_WORKSPACE;
   // ROW and MERGE stream col_packed and val with bulk copies: 16-byte aligned bases
   if ((v == CMRS_VARIANT_ROW || v == CMRS_VARIANT_MERGE) && A->nnz > 0 &&
@@ -1710,7 +1760,7 @@ extern "C" int cmrs_spmv_noalloc(const cmrs_matrix *A, const void *x, void *y, v
   if (A->flags & (CMRS_SORTED | CMRS_PADDED)) return CMRS_ERR_UNSUPPORTED;
   if (A->rows == 0) return CMRS_OK;
   if (!y || (A->nnz > 0 && !x)) return CMRS_ERR_ARG;
-  if (merge_ws_bytes(A->nnz) > kNoAllocBytes) return CMRS_ERR_WORKSPACE;
+  if (merge_ws_bytes(A->nnz, A->dtype) > kNoAllocBytes) return CMRS_ERR_WORKSPACE;
   if (A->nnz > 0 && ((reinterpret_cast<uintptr_t>(A->col_packed) | reinterpret_cast<uintptr_t>(A->val)) & 15))
     return CMRS_ERR_ARG;
   void *scratch = nullptr;

@@ -71,6 +71,16 @@ def test_host_validation_paths(L):
     assert L.cmrs_spmv_workspace(ctypes.byref(m), 0, ctypes.byref(n)) == 1
     m.strips, m.bits = 3, 5
     assert L.cmrs_spmv_workspace(ctypes.byref(m), 0, ctypes.byref(n)) == 1
+    # MERGE's workspace at the no-alloc entry point's stated limits: exactly
+    # its 2 MiB fixed array, one entry more needs another tile
+    m.rows, m.cols, m.height, m.bits = 1 << 20, 1 << 20, 4, 4
+    m.strips = (m.rows + 3) // 4
+    for dtype, limit in ((0, 67_092_480), (1, 82_001_920), (2, 82_001_920), (3, 82_001_920)):
+        m.dtype = dtype
+        m.nnz = limit
+        assert L.cmrs_spmv_workspace(ctypes.byref(m), 2, ctypes.byref(n)) == 0 and n.value == 2 << 20
+        m.nnz = limit + 1
+        assert L.cmrs_spmv_workspace(ctypes.byref(m), 2, ctypes.byref(n)) == 0 and n.value > 2 << 20
     # the wait probe checks its workspace and try count before any launch
     assert L.cmrs_wait_probe(None, 0, 0, None) == 1  # tries checked before the fixed array is looked up
     assert L.cmrs_wait_probe(ctypes.c_void_p(4096 + 16), 16, 0, None) == 1
@@ -260,3 +270,14 @@ def test_padded_split_workspace(L):
     assert ws(strips=10, passes=40) == 256                # short strips: one warp per strip
     assert ws(strips=200000, passes=64) == 256            # more strips than two per resident warp
     assert ws(strips=10, passes=4096, flags=0) == 256     # plain CMRS, ROW
+
+
+def test_binding_checks_tensor_operands_on_the_host():
+    """The C ABI takes bare pointers; the Python binding checks each tensor
+    (device, value type, contiguity, length) before its pointer goes."""
+    import torch
+    from paper_1203_2946_gb300 import binding as b
+    with pytest.raises(TypeError):
+        b._operand(torch.zeros(4, dtype=torch.float64), torch.float64, 4, "x")  # host memory
+    with pytest.raises(TypeError):
+        b._operand(None, torch.float64, 4, "x")

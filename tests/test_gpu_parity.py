@@ -262,6 +262,29 @@ def test_spmv_degenerate(b):
     assert b.cmrs_spmv(M, torch.ones(5, dtype=torch.float64, device="cuda")).numel() == 0
 
 
+def test_binding_rejects_mismatched_operands(b):
+    """x or y of another value type, too short, or strided: refused by the
+    binding before any pointer reaches the library (an FP32 x given to an
+    FP64 matrix would be read as half as many doubles, past its end)."""
+    a = inputs.random_csr(300, 200, 0.05, seed=1)
+    M = convert(b, a, 4)  # FP64
+    x64 = torch.ones(a.cols, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        b.cmrs_spmv(M, x64.float())
+    with pytest.raises(ValueError):
+        b.cmrs_spmv(M, x64[:-1])
+    with pytest.raises(ValueError):
+        b.cmrs_spmv(M, torch.ones(2 * a.cols, dtype=torch.float64, device="cuda")[::2])
+    with pytest.raises(TypeError):
+        b.cmrs_spmv(M, x64, torch.empty(a.rows, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        b.cmrs_spmv(M, x64, torch.empty(a.rows - 1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError):
+        b.cmrs_spmv_noalloc(M, x64.float())
+    y = b.cmrs_spmv(M, x64)  # the well-formed call still runs
+    assert y.shape == (a.rows,)
+
+
 def test_spmv_repeatable(b):
     a = inputs.powerlaw_rows(50000, 2.1, 20000, seed=4)
     x = xvec(a, 1)

@@ -8,8 +8,8 @@ through the C ABI:
   the other forms within (len_i + 2) 2^-24 (|A_q||x_q|)_i of the
   quantised-input oracle) and bit for bit against cmrs_spmv with MERGE and a
   caller workspace, on two calls in a row;
-- on a matrix at the array's limit (111,820,800 entries), so that its last
-  tiles are written and read;
+- on a matrix at the array's limit (82,001,920 entries in FP32), so that its
+  last tiles are written and read;
 - with the device's allocated bytes unchanged across calls;
 - with its status query, which reports a bounded wait that gave up.
 
@@ -27,7 +27,10 @@ from paper_1203_2946_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-LIMIT_NNZ = 111_820_800  # 58,240 tiles of 1,920 entries: the fixed array's capacity
+# the fixed array's capacity: 58,240 MERGE tiles, of 1,152 entries in FP64 and
+# 1,408 in the other forms
+LIMIT_NNZ_F64 = 67_092_480
+LIMIT_NNZ = 82_001_920
 
 
 @pytest.fixture(scope="module")
@@ -152,8 +155,10 @@ def test_noalloc_rejects_matrix_past_its_limit(b):
     m = b.cmrs_matrix()
     m.rows, m.cols, m.height, m.bits, m.dtype = 1 << 20, 1 << 20, 4, 4, 0
     m.strips = (m.rows + 3) // 4
-    m.nnz = LIMIT_NNZ + 1  # one tile more than the fixed scratch holds
     m.strip_ptr = m.col_packed = m.val = 256
     x = torch.empty(1, device="cuda")
-    assert b.lib().cmrs_spmv_noalloc(ctypes.byref(m), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()),
-                                     None) == 7
+    for dtype, limit in ((0, LIMIT_NNZ_F64), (1, LIMIT_NNZ)):
+        m.dtype = dtype
+        m.nnz = limit + 1  # one tile more than the fixed scratch holds
+        assert b.lib().cmrs_spmv_noalloc(ctypes.byref(m), ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(x.data_ptr()), None) == 7
