@@ -34,6 +34,31 @@ constexpr int kRowCap = 32 * CMRS_ROW_ROWS;   // ROW: entries per shared-memory 
 // further 8 KB of shared memory per CTA, leaving 28 KB, took the power-law
 // FP32 product from 143 to 222 us.  FP32: 11 entries at 6 CTAs (80
 // registers); FP64: 9 at 5 CTAs (96 registers); both keep 92 KB of L1.
+// Matrices whose rows average CMRS_MERGE_LONG_MU entries or more pay for
+// MERGE's per-tile joins more than for L1 misses: they take the _LONG tiles,
+// 15 entries a thread at as many CTAs as fit (dense 10^4 x 10^4 as sparse:
+// FP64 425 us against 486 us with the short tiles, FP32 257 against 287).
+#ifndef CMRS_MERGE_LONG_MU
+#define CMRS_MERGE_LONG_MU 16
+#endif
+#ifndef CMRS_MERGE_E_F64_LONG
+#define CMRS_MERGE_E_F64_LONG 15
+#endif
+#ifndef CMRS_MERGE_MINB_F64_LONG
+#define CMRS_MERGE_MINB_F64_LONG 4
+#endif
+#ifndef CMRS_MERGE_CTAS_F64_LONG
+#define CMRS_MERGE_CTAS_F64_LONG 0
+#endif
+#ifndef CMRS_MERGE_E_F32_LONG
+#define CMRS_MERGE_E_F32_LONG 15
+#endif
+#ifndef CMRS_MERGE_MINB_F32_LONG
+#define CMRS_MERGE_MINB_F32_LONG 5
+#endif
+#ifndef CMRS_MERGE_CTAS_F32_LONG
+#define CMRS_MERGE_CTAS_F32_LONG 0
+#endif
 #ifndef CMRS_MERGE_E_F64
 #define CMRS_MERGE_E_F64 9
 #endif
@@ -65,14 +90,25 @@ constexpr bool kMergeVSmem = CMRS_MERGE_VSMEM != 0;
 #ifndef CMRS_LANE_CTAS
 #define CMRS_LANE_CTAS 0
 #endif
-template <int DT>
+template <int DT, bool kLong>
 struct MergeCfg {
-  static constexpr int E = DT == CMRS_F64 ? CMRS_MERGE_E_F64 : CMRS_MERGE_E_F32;
+  static constexpr bool F64 = DT == CMRS_F64;
+  static constexpr int E = F64 ? (kLong ? CMRS_MERGE_E_F64_LONG : CMRS_MERGE_E_F64)
+                               : (kLong ? CMRS_MERGE_E_F32_LONG : CMRS_MERGE_E_F32);
   static constexpr int Tile = kMergeThreads * E;  // entries per tile, a multiple of 8
-  static constexpr int MinBlocks = DT == CMRS_F64 ? CMRS_MERGE_MINB_F64 : CMRS_MERGE_MINB_F32;
-  static constexpr int Ctas = DT == CMRS_F64 ? CMRS_MERGE_CTAS_F64 : CMRS_MERGE_CTAS_F32;
+  static constexpr int MinBlocks = F64 ? (kLong ? CMRS_MERGE_MINB_F64_LONG : CMRS_MERGE_MINB_F64)
+                                       : (kLong ? CMRS_MERGE_MINB_F32_LONG : CMRS_MERGE_MINB_F32);
+  static constexpr int Ctas = F64 ? (kLong ? CMRS_MERGE_CTAS_F64_LONG : CMRS_MERGE_CTAS_F64)
+                                  : (kLong ? CMRS_MERGE_CTAS_F32_LONG : CMRS_MERGE_CTAS_F32);
   static_assert(E % 2 == 1 && Tile % 8 == 0, "MERGE: odd entries per thread, 8-entry-aligned tiles");
 };
+// the long-row tiles are a second kernel only where they differ
+template <int DT>
+constexpr bool merge_long_differs() {
+  return MergeCfg<DT, true>::E != MergeCfg<DT, false>::E ||
+         MergeCfg<DT, true>::MinBlocks != MergeCfg<DT, false>::MinBlocks ||
+         MergeCfg<DT, true>::Ctas != MergeCfg<DT, false>::Ctas;
+}
 constexpr int kMergeWarps = kMergeThreads / 32;
 constexpr int kStripWarps = 8;
 constexpr int kStages = 2;
@@ -736,7 +772,8 @@ __global__ void __launch_bounds__(kPadWarps * 32, CMRS_PAD_MINB) k_spmv_padded(i
 
 // ============================================================== MERGE mapping
 // Tile t = entries [T t, T t + T), T = 128 E, staged by bulk copies; thread i
-// owns the E consecutive entries from T t + E i (E = 9 for FP64, 11 else).  It finds their strip by
+// owns the E consecutive entries from T t + E i (E = 9 for FP64, 11 for the
+// other forms, 15 for both where rows average 16 entries or more).  It finds their strip by
 // a binary search of StripPtr between the strips holding the tile's first
 // and next tile's first entry (tile_strip[], one small pre-pass), then walks
 // the entries: a row's run is summed by one FMA chain; a run that starts and
@@ -755,8 +792,8 @@ __global__ void k_tile_map(int strips, const int32_t *__restrict__ sp, int tile,
   for (long long t = (a + tile - 1) / tile; t * tile < b && t < ntiles; ++t) tile_strip[t] = s;
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kMergeThreads, MergeCfg<DT>::MinBlocks)
+template <int DT, bool kLong>
+__global__ void __launch_bounds__(kMergeThreads, (MergeCfg<DT, kLong>::MinBlocks))
     k_spmv_merge(int rows, int height, int bits, int strips, int nnz,
                                                               const int32_t *__restrict__ sp,
                                                               const uint32_t *__restrict__ packed,
@@ -768,7 +805,7 @@ __global__ void __launch_bounds__(kMergeThreads, MergeCfg<DT>::MinBlocks)
                                                               TileRec *__restrict__ recs, uint32_t *status) {
   typedef typename Form<DT>::Stored S;
   typedef typename Form<DT>::Acc A;
-  constexpr int kMergeE = MergeCfg<DT>::E, kMergeTile = MergeCfg<DT>::Tile;
+  constexpr int kMergeE = MergeCfg<DT, kLong>::E, kMergeTile = MergeCfg<DT, kLong>::Tile;
   extern __shared__ __align__(128) char smem[];
   __shared__ uint64_t bars[kStages];
   __shared__ StageInfo info[kStages];
@@ -1370,8 +1407,11 @@ int occupancy(K kernel, int threads, size_t smem, Occ &cache, size_t smem_cap = 
   return cache.val[dev];
 }
 
+// sized for the smaller of the form's two tiles: enough for either launch
 size_t merge_ws_bytes(int nnz, int dtype) {
-  const long long ntiles = ceil_div(nnz, dtype == CMRS_F64 ? MergeCfg<CMRS_F64>::Tile : MergeCfg<CMRS_F32>::Tile);
+  const int tile = dtype == CMRS_F64 ? std::min(MergeCfg<CMRS_F64, false>::Tile, MergeCfg<CMRS_F64, true>::Tile)
+                                     : std::min(MergeCfg<CMRS_F32, false>::Tile, MergeCfg<CMRS_F32, true>::Tile);
+  const long long ntiles = ceil_div(nnz, tile);
   return 256 + align256((size_t)(ntiles + 1) * 4) + align256((size_t)ntiles * sizeof(TileRec));
 }
 
@@ -1442,6 +1482,28 @@ int launch_padded(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, con
   return CMRS_OK;
 }
 
+// MERGE: tile map, the product, the fix-up of rows cut by tile boundaries
+template <int DT, bool kLong>
+int launch_merge(const cmrs_matrix *A, const typename Form<DT>::Stored *hi, const typename Form<DT>::Stored *lo,
+                 const typename Form<DT>::Acc *x, typename Form<DT>::Acc *y, uint32_t *status, char *ws,
+                 cudaStream_t st) {
+  typedef typename Form<DT>::Acc Acc;
+  static Occ occ;
+  constexpr int kMergeTile = MergeCfg<DT, kLong>::Tile;
+  const int ntiles = (int)ceil_div(A->nnz, kMergeTile);
+  int32_t *tile_strip = reinterpret_cast<int32_t *>(ws + 256);
+  TileRec *recs = reinterpret_cast<TileRec *>(ws + 256 + align256((size_t)(ntiles + 1) * 4));
+  k_tile_map<<<(int)ceil_div(A->strips, 256), 256, 0, st>>>(A->strips, A->strip_ptr, kMergeTile, ntiles, tile_strip);
+  CMRS_LAUNCH_CHECK();
+  const size_t smem = kStages * Stage<DT>::bytes(kMergeTile);
+  const int per_sm = occupancy(k_spmv_merge<DT, kLong>, kMergeThreads, smem, occ, 0, MergeCfg<DT, kLong>::Ctas);
+  const int grid = (int)std::min<long long>(ntiles, (long long)per_sm * sm_count());
+  int rc = launch_pdl(k_spmv_merge<DT, kLong>, (unsigned)grid, kMergeThreads, smem, st, A->rows, A->height, A->bits,
+                      A->strips, A->nnz, A->strip_ptr, A->col_packed, hi, lo, x, y, tile_strip, ntiles, recs, status);
+  if (rc) return rc;
+  return launch_pdl(k_merge_fixup<Acc>, (unsigned)ceil_div(ntiles, 256), 256, 0, st, ntiles, A->rows, recs, y);
+}
+
 template <int DT>
 int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_map, int variant, char *ws,
            size_t ws_bytes, cudaStream_t st) {
@@ -1509,21 +1571,11 @@ int launch(const cmrs_matrix *A, const void *xv, void *yv, const int32_t *row_ma
       default: return launch_padded<DT, 8>(A, hi, lo, x, y, row_map, status, ws, ws_bytes, st);
     }
   } else {
-    static Occ occ;
-    constexpr int kMergeTile = MergeCfg<DT>::Tile;
-    const int ntiles = (int)ceil_div(A->nnz, kMergeTile);
-    int32_t *tile_strip = reinterpret_cast<int32_t *>(ws + 256);
-    TileRec *recs = reinterpret_cast<TileRec *>(ws + 256 + align256((size_t)(ntiles + 1) * 4));
-    k_tile_map<<<(int)ceil_div(A->strips, 256), 256, 0, st>>>(A->strips, A->strip_ptr, kMergeTile, ntiles, tile_strip);
-    CMRS_LAUNCH_CHECK();
-    const size_t smem = kStages * Stage<DT>::bytes(kMergeTile);
-    const int per_sm = occupancy(k_spmv_merge<DT>, kMergeThreads, smem, occ, 0, MergeCfg<DT>::Ctas);
-    const int grid = (int)std::min<long long>(ntiles, (long long)per_sm * sms);
-    int rc = launch_pdl(k_spmv_merge<DT>, (unsigned)grid, kMergeThreads, smem, st, A->rows, A->height, A->bits,
-                        A->strips, A->nnz, A->strip_ptr, A->col_packed, hi, lo, x, y, tile_strip, ntiles, recs, status);
-    if (rc) return rc;
-    rc = launch_pdl(k_merge_fixup<Acc>, (unsigned)ceil_div(ntiles, 256), 256, 0, st, ntiles, A->rows, recs, y);
-    if (rc) return rc;
+    if constexpr (merge_long_differs<DT>()) {
+      if ((double)A->nnz >= CMRS_MERGE_LONG_MU * (double)A->rows)
+        return launch_merge<DT, true>(A, hi, lo, x, y, status, ws, st);
+    }
+    return launch_merge<DT, false>(A, hi, lo, x, y, status, ws, st);
   }
   return CMRS_OK;
 }
