@@ -262,6 +262,27 @@ def test_spmv_degenerate(b):
     assert b.cmrs_spmv(M, torch.ones(5, dtype=torch.float64, device="cuda")).numel() == 0
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_merge_tile_sets_either_side_of_the_row_length_bound(b, dtype):
+    """MERGE launches 9- (FP64) or 11-entry tiles where rows average fewer
+    than 16 entries and 15-entry tiles from 16 on: rows of exactly 16 and
+    just under, with empty rows, a row longer than several tiles and a ragged
+    tail, both sides of the bound, against the oracle."""
+    rng = np.random.default_rng(40 + dtype)
+    for target in (15.9, 16.0):
+        L = rng.integers(0, 32, 30011)
+        L[100:140] = 0
+        L[7] = 5000
+        L[-1] = 3
+        L[8] += int(round(target * L.size)) - int(L.sum())  # mean exactly `target` (to rounding)
+        assert L[8] >= 0
+        a = inputs.from_lengths(L, 40000, seed=11 + dtype, dtype=np.float64)
+        assert (a.nnz >= 16 * a.rows) == (target >= 16.0)
+        x = xvec(a, dtype)
+        for h in (1, 32):
+            check_spmv(b, convert(b, a, h, False, dtype), a, x, 2, dtype)
+
+
 def test_binding_rejects_mismatched_operands(b):
     """x or y of another value type, too short, or strided: refused by the
     binding before any pointer reaches the library (an FP32 x given to an
