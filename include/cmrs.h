@@ -300,11 +300,12 @@ int cmrs_spmv_rows(const cmrs_matrix *A, const void *x, void *y, const int32_t *
  * file-scope __device__ array, resident on every GPU that loads the library
  * until the process exits).  Limit: 58,240 MERGE tiles, i.e. A->nnz <=
  * 67,092,480 for CMRS_F64 (tiles of 1,152 entries) and <= 82,001,920 for the
- * other forms (1,408 entries); larger matrices return CMRS_ERR_WORKSPACE before any device
- * work.  Unsorted, unpadded strips only (CMRS_ERR_UNSUPPORTED otherwise).  No
- * cudaMalloc, cudaFree or other allocating call is made.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current), so make that first call before any stream capture.
+ * other forms (1,408 entries); larger matrices return CMRS_ERR_WORKSPACE
+ * before any device work.  Unsorted, unpadded strips only
+ * (CMRS_ERR_UNSUPPORTED otherwise).  No cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current)
+ * and keeps it for the later calls.
  * Every call shares the one array, which keeps the last call's contents:
  * calls that may overlap on the GPU (two streams, two host threads) race and
  * their results are undefined.  The cached address belongs to the device's
